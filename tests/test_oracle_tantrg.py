@@ -1,0 +1,204 @@
+"""Pins of the dense tanTRG oracle (integrator, Lanczos, gauge, truncation).
+
+The strongest pin is tangent-space exactness (Supplement, "Splitting method"):
+with bond dimensions at their maximum the 1-TDVP/2-TDVP integrators carry no
+projection error, so the oracle must reproduce exact diagonalisation of the
+same initial state, exp(-(beta-beta0) H/2)(I - beta0 H/2), to rounding and
+Krylov error.  Planted mistakes (wrong step length, wrong bond-step sign)
+must break it.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import model as om
+from oracle import mpo as ompo
+from oracle import tantrg as tt
+
+KEYS = ("lnZ", "energy_per_site", "density", "double_occ")
+
+
+def _rel(a, b):
+    return abs(a - b) / max(1e-300, abs(b))
+
+
+def _run_vs_ed(m, D, beta_end, tol, beta0=0.01, dtau=0.05):
+    W = ompo.hubbard_mpo(m)
+    st = tt.run(W, beta0, dtau, beta_end, tt.TruncOpts(D))
+    ob = tt.measure(st)
+    ed = om.ed_thermo(m, [st.beta], beta0=beta0)[0]
+    for k in KEYS:
+        assert _rel(ob[k], ed[k]) < tol, (k, ob[k], ed[k])
+    return st, ob
+
+
+def test_full_rank_chain_matches_ed():
+    """3-site open chain, bonds at their maximum (16, 16): exact up to Krylov error."""
+    m = om.Model(1, 3, False, U=3.0, mu=0.4, form=0)
+    st, _ = _run_vs_ed(m, 16, 1.51, 1e-10)
+    assert st.bond_dims() == [16, 16]
+    assert tt.hermiticity_defect(st) < 1e-7
+
+
+@pytest.mark.slow
+def test_full_rank_2x2_matches_ed():
+    """2x2 cluster of the first workload (U=4, PH form, mu=0) untruncated (D=256)."""
+    m = om.Model(2, 2, False, U=4.0, mu=0.0, form=1)
+    st, ob = _run_vs_ed(m, 256, 0.51, 1e-10)
+    assert st.bond_dims() == [16, 256, 16]
+    assert abs(ob["density"] - 1.0) < 1e-10  # half filling at PH-symmetric mu = 0
+
+
+def test_planted_wrong_step_length_is_caught(monkeypatch):
+    """tau = dtau/2 per half sweep (instead of dtau/4) must break the ED pin."""
+    real = tt.tdvp1_step
+
+    def broken(st, dtau, K=8):
+        tt.tdvp1_sweep_lr(st, dtau / 2, K)
+        tt.tdvp1_sweep_rl(st, dtau / 2, K)
+        st.beta += dtau
+
+    monkeypatch.setattr(tt, "tdvp1_step", broken)
+    m = om.Model(1, 3, False, U=3.0, mu=0.4, form=0)
+    W = ompo.hubbard_mpo(m)
+    st = tt.run(W, 0.01, 0.05, 0.51, tt.TruncOpts(16))
+    ob = tt.measure(st)
+    ed = om.ed_thermo(m, [st.beta], beta0=0.01)[0]
+    assert _rel(ob["lnZ"], ed["lnZ"]) > 1e-3
+    monkeypatch.setattr(tt, "tdvp1_step", real)
+
+
+def test_planted_wrong_bond_sign_is_caught(monkeypatch):
+    """The backward bond step exp(+tau H0) taken forward breaks exactness."""
+    real = tt._bond_exp
+
+    def broken(st, k, S, t, K):
+        return real(st, k, S, -t, K)
+
+    monkeypatch.setattr(tt, "_bond_exp", broken)
+    m = om.Model(1, 3, False, U=3.0, mu=0.4, form=0)
+    W = ompo.hubbard_mpo(m)
+    st = tt.run(W, 0.01, 0.05, 0.51, tt.TruncOpts(16))
+    ob = tt.measure(st)
+    ed = om.ed_thermo(m, [st.beta], beta0=0.01)[0]
+    assert _rel(ob["energy_per_site"], ed["energy_per_site"]) > 1e-4
+
+
+def test_initial_state_is_first_order_expansion():
+    """rho_h(beta0) = I - beta0 H / 2: ln Z and E at beta0 from the dense matrix."""
+    m = om.Model(2, 2, False, U=4.0, mu=0.3, form=0)
+    H = om.dense_hamiltonian(m).toarray()
+    b0 = 0.02
+    rho = np.eye(len(H)) - 0.5 * b0 * H
+    st = tt.init_state(ompo.hubbard_mpo(m), b0)
+    ob = tt.measure(st)
+    Z = np.sum(rho * rho)
+    assert abs(ob["lnZ"] - math.log(Z)) < 1e-12
+    assert abs(ob["energy_per_site"] - np.trace(rho @ H @ rho) / Z / m.N) < 1e-12
+    # right canonical form: sum_s A^s A^s^T = 1 on every site but the first
+    for A in st.A[1:]:
+        Dl = A.shape[0]
+        M = A.reshape(Dl, -1)
+        assert np.allclose(M @ M.T, np.eye(Dl), atol=1e-12)
+
+
+def test_lanczos_full_krylov_is_exact():
+    """K = dim: the Lanczos exponential equals the matrix exponential."""
+    rng = np.random.default_rng(7)
+    n = 12
+    X = rng.standard_normal((n, n))
+    H = 0.5 * (X + X.T)
+    v = rng.standard_normal(n)
+    for t in (-0.3, 0.2):
+        y, _ = tt.lanczos_expm(lambda x: H @ x, v, t, n)
+        ref = scipy.linalg.expm(t * H) @ v
+        assert np.abs(y - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_lanczos_truncated_krylov_error_and_estimate():
+    """Fixed K < dim: error shrinks fast with K and the a-posteriori estimate
+    bounds it within an order of magnitude."""
+    rng = np.random.default_rng(3)
+    n = 200
+    X = rng.standard_normal((n, n)) / math.sqrt(n)
+    H = X + X.T
+    v = rng.standard_normal(n)
+    t = -0.1
+    ref = scipy.linalg.expm(t * H) @ v
+    errs = []
+    for K in (4, 6, 8):
+        y, est = tt.lanczos_expm(lambda x: H @ x, v, t, K)
+        err = np.linalg.norm(y - ref)
+        errs.append(err)
+        assert err < 10 * est + 1e-14
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 1e-9 * np.linalg.norm(v)
+
+
+def test_lanczos_breakdown_on_eigenvector():
+    """An eigenvector spans an invariant subspace: exp(tH) v = exp(t lambda) v."""
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((20, 20))
+    H = X + X.T
+    lam, V = np.linalg.eigh(H)
+    v = 3.0 * V[:, 5]
+    y, _ = tt.lanczos_expm(lambda x: H @ x, v, -0.2, 8)
+    assert np.abs(y - math.exp(-0.2 * lam[5]) * v).max() < 1e-12
+
+
+def test_qr_and_lq_gauges():
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((3, 4, 4, 7))
+    Al, S = tt.qr_left(A)
+    M = Al.reshape(-1, Al.shape[3])
+    assert np.allclose(M.T @ M, np.eye(M.shape[1]), atol=1e-13)
+    assert np.allclose(np.tensordot(Al, S, axes=([3], [0])), A, atol=1e-13)
+    assert np.all(np.diag(S) >= 0)
+    Ar, S2 = tt.lq_right(A)
+    M = Ar.reshape(Ar.shape[0], -1)
+    assert np.allclose(M @ M.T, np.eye(M.shape[0]), atol=1e-13)
+    assert np.allclose(np.tensordot(S2, Ar, axes=([1], [0])), A, atol=1e-13)
+    assert np.all(np.diag(S2) >= 0)
+
+
+def test_truncation_rule():
+    s = np.array([1.0, 0.5, 0.5, 0.25, 0.1, 1e-15])
+    assert tt.truncation_rank(s, 10, 1e-14, 1e-10) == 5       # drop below svd_cut
+    assert tt.truncation_rank(s, 2, 1e-14, 1e-10) == 1        # never split 0.5, 0.5
+    assert tt.truncation_rank(s, 3, 1e-14, 1e-10) == 3
+    s2 = np.array([0.7, 0.7, 0.7, 0.1])
+    assert tt.truncation_rank(s2, 2, 1e-14, 1e-10) == 3       # leading group kept whole
+    s3 = np.array([1.0, 1e-9, 1e-9 * (1 + 1e-7), 1e-12])
+    assert tt.truncation_rank(s3, 2, 0.0, 1e-10) == 1         # absolute guard groups them
+
+
+def test_free_fermion_ladder_error_decreases_with_D():
+    """Fig. 1(c)-style benchmark at U=0: the free-energy error against the exact
+    solution is small and shrinks as D grows."""
+    m = om.Model(3, 2, False, U=0.0, mu=0.0, form=1)
+    W = ompo.hubbard_mpo(m)
+    exact = om.ed_thermo(m, [1.01], beta0=0.01)[0]
+    errs = []
+    for D in (8, 24):
+        st = tt.run(W, 0.01, 0.05, 1.01, tt.TruncOpts(D))
+        ob = tt.measure(st)
+        errs.append(_rel(ob["free_energy_per_site"], exact["free_energy_per_site"]))
+    assert errs[1] < 0.5 * errs[0] < 0.05
+
+
+def test_thermodynamic_invariants_along_a_truncated_run():
+    """Along a truncated run: dlnZ/dbeta = -E to O(dtau^2), E non-increasing,
+    f non-decreasing (df/dT = -S <= 0)."""
+    m = om.Model(3, 2, False, U=4.0, mu=0.5, form=1)
+    W = ompo.hubbard_mpo(m)
+    rec = []
+    tt.run(W, 0.01, 0.05, 0.81, tt.TruncOpts(16), callback=lambda st, _: rec.append(tt.measure(st)))
+    E = np.array([r["energy_per_site"] for r in rec])
+    f = np.array([r["free_energy_per_site"] for r in rec])
+    lnZ = np.array([r["lnZ"] for r in rec])
+    assert np.all(np.diff(E) < 1e-9)
+    assert np.all(np.diff(f) > -1e-9)
+    dlnz = (lnZ[2:] - lnZ[:-2]) / (2 * 0.05)
+    assert np.abs(-dlnz / m.N - E[1:-1]).max() < 2e-3
