@@ -1,0 +1,209 @@
+/*
+ * tantrg.h - C ABI of the GB300 tanTRG library (libtantrg.so).
+ *
+ * Tangent-space tensor renormalization group (arXiv 2212.11973): finite-
+ * temperature imaginary-time evolution of the MPO half-density operator
+ * rho_h(beta) = exp(-beta H / 2) of the 2D Hubbard model (Eq. 3) on a
+ * snake-ordered cylinder or ladder (Fig. 1(a)), by 1-site TDVP sweeps
+ * (Eq. 2; Supplement, "Procedure of 1-TDVP") after a 2-site TDVP growth
+ * stage (Supplement, "2-TDVP in the initial stage").
+ *
+ * Conventions
+ *   - Local basis sigma = n_up + 2 n_dn = {|0>, |up>, |dn>, |up dn>}, with
+ *     |up dn> = c+_up c+_dn |0>; Jordan-Wigner strings run along the snake.
+ *   - rho_h is stored as its Choi super-MPS (Supplement, "Choi
+ *     transformation"): site tensors A[a_l, (sigma, sigma'), a_r], U(1) x U(1)
+ *     block sparse in (particle number, 2 Sz).  Every tensor is real.
+ *   - Z(beta) = <<rho_h|rho_h>>, E = <<rho_h|H x I|rho_h>> / Z (bilayer trick,
+ *     Supplement eq. for E(beta)).
+ *   - One beta-step of size dtau is a left-to-right plus a right-to-left half
+ *     sweep, each integrating with tau = dtau / 4, so rho_h -> exp(-dtau H/2)
+ *     rho_h (symmetric Lie-Trotter composition; main text "4 tau = 1").
+ *
+ * Ownership and errors
+ *   - Every object belongs to one context and runs on the context's CUDA
+ *     stream.  The caller owns every handle it receives and frees it with the
+ *     matching _destroy call (destroy on NULL is a no-op).
+ *   - Functions return tt_status; no C++ exception crosses the ABI.  After an
+ *     error the message is available from tt_last_error(ctx); an object that
+ *     saw a CUDA or numeric error is poisoned: later calls on it return
+ *     TT_ERR_STATE, destroying it is always safe.
+ *   - Pointers documented as "host" are read or written by the CPU before the
+ *     call returns; pointers documented as "device" are cudaMalloc'ed memory of
+ *     the context's device and are only read/written in stream order.
+ */
+#ifndef TANTRG_H
+#define TANTRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_OK = 0,
+  TT_ERR_INVALID_ARG = 1, /* bad size, geometry, option or NULL pointer */
+  TT_ERR_OOM = 2,         /* device allocation failed */
+  TT_ERR_CUDA = 3,        /* a CUDA runtime / library call failed */
+  TT_ERR_NUMERIC = 4,     /* NaN/Inf or a failed factorisation was detected */
+  TT_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  TT_ERR_STATE = 6        /* object poisoned by an earlier error, or wrong stage */
+} tt_status;
+
+typedef enum {
+  TT_PREC_FP64 = 0,          /* every contraction in FP64 */
+  TT_PREC_MIXED_BF16X3 = 1,  /* H_eff and environment contractions as split-
+                                BF16 tensor-core products, 2 levels / 3
+                                products (~2^-16 relative) */
+  TT_PREC_MIXED_BF16X6 = 2   /* 3 levels / 6 products (~2^-24 relative), FP32
+                                accumulation folded per K chunk into a two-
+                                float sum.  In both mixed modes the Lanczos
+                                vectors, Krylov exponential, QR, SVD, absorb
+                                step, measurements and log-norm stay FP64 */
+} tt_precision;
+
+typedef struct tt_ctx tt_ctx;
+typedef struct tt_mpo tt_mpo;
+typedef struct tt_rho tt_rho;
+typedef struct tt_batch tt_batch;
+
+/* Optional device allocator (e.g. PyTorch's caching allocator).  alloc must
+ * return device memory usable on `stream` (NULL on failure); free releases it. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} tt_alloc_cb;
+
+/* Hubbard model, Eq. 3.  interaction_form 0: U n_up n_dn (Eq. 3);
+ * 1: U (n_up - 1/2)(n_dn - 1/2), the particle-hole symmetric form of the DQMC
+ * appendix (mu = 0 is half filling).  Lx >= 1 columns (open), Wy >= 1 rows;
+ * bc_y_periodic wraps y when Wy > 2.  tp (next-nearest hopping, Eq. S1) must be
+ * 0 in this version.  Lx * Wy <= 512. */
+typedef struct {
+  int Lx, Wy, bc_y_periodic;
+  double t, tp, U, mu;
+  int interaction_form;
+} tt_model;
+
+typedef struct {
+  int D_max;            /* bond dimension cap (U(1)xU(1) states), >= 1 */
+  int krylov_dim;       /* Lanczos Krylov dimension K, 1..16 (paper: K small) */
+  int precision;        /* tt_precision of the 1-TDVP linear stage */
+  int growth_precision; /* tt_precision of the 2-TDVP growth; -1 = FP64.  Mixed
+                           growth perturbs exactly degenerate singular values
+                           and so the truncation; use FP64 for parity runs */
+  double svd_cut;       /* growth: drop s <= svd_cut * s_max (default 1e-12) */
+  double degen_tol;     /* growth: never split s_k, s_k+1 with
+                           s_k - s_k+1 <= degen_tol s_k + 1e-14 s_max (1e-10) */
+} tt_run_opts;
+
+typedef struct {
+  double beta;                 /* inverse temperature reached */
+  double energy_per_site;      /* <<rho_h|H x I|rho_h>> / (N Z) */
+  double density;              /* (1/N) sum_i <n_i> */
+  double double_occ;           /* D_n = (1/N) sum_i <n_i,up n_i,dn> */
+  double free_energy_per_site; /* -ln Z / (beta N), grand potential per site */
+  double lnZ;                  /* ln Z = 2 logscale + ln <<psi|psi>> */
+  int max_bond;                /* largest bond dimension */
+  double krylov_resid_max;     /* max over updates of ||v|| beta_K |c_K| */
+} tt_obs;
+
+typedef struct {
+  double heff_flops;       /* algorithmic flops of the site H_eff applies of the last tt_tdvp_step */
+  double heff_ms;          /* summed device time of those applies (CUDA events) */
+  double step_flops;       /* algorithmic flops of all contractions of the last step */
+  double step_ms;          /* device time of the last step */
+  double bytes_lanczos;    /* algorithmic bytes moved by Lanczos vector kernels, last step */
+  double lanczos_ms;       /* their device time */
+  long long launches;      /* kernels launched by the last step */
+  int n_sites, max_bond, n_sectors_max;
+} tt_stats;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* alloc may be NULL (then cudaMallocAsync on the stream).  cuda_stream is a
+ * cudaStream_t of the current device or NULL for the legacy default stream. */
+tt_status tt_ctx_create(const tt_alloc_cb* alloc, void* cuda_stream, tt_ctx** out);
+void tt_ctx_destroy(tt_ctx* ctx);
+/* Message of the last failed call on this context ("" if none).  Owned by ctx. */
+const char* tt_last_error(const tt_ctx* ctx);
+
+/* ---- Hubbard MPO (Eq. 3; built on the host as a finite automaton with
+ *      U(1)xU(1) labels on every leg, uploaded to the device) --------------- */
+tt_status tt_hubbard_mpo_create(tt_ctx* ctx, const tt_model* m, tt_mpo** out);
+void tt_mpo_destroy(tt_mpo* mpo);
+/* Number of sites and the MPO bond dimension of bond k (0..N). */
+int tt_mpo_num_sites(const tt_mpo* mpo);
+int tt_mpo_bond_dim(const tt_mpo* mpo, int k);
+
+/* ---- state ------------------------------------------------------------- */
+
+/* rho_h(beta0) = I - beta0 H / 2 (main text: rho_0 = 1 - tau_0 H from the MPO
+ * of H), right-canonicalised by LQ sweeps (canonical centre on site 0).
+ * taylor_order must be 1 in this version. */
+tt_status tt_rho_create(tt_ctx* ctx, const tt_mpo* mpo, double beta0, int taylor_order,
+                        const tt_run_opts* opts, tt_rho** out);
+void tt_rho_destroy(tt_rho* rho);
+
+/* 2-TDVP growth stage: beta-steps of size dtau until every bond holds
+ * min(D_max, 16^k, 16^(N-k)) states or beta >= beta_max.  Writes the beta
+ * reached to *beta_reached (host, may be NULL).  Synchronises the stream. */
+tt_status tt_rho_grow(tt_rho* rho, const tt_mpo* mpo, double dtau, double beta_max,
+                      double* beta_reached);
+
+/* n_steps 1-TDVP beta-steps of size dtau.  Asynchronous on the ctx stream;
+ * the block structure is fixed during the call. */
+tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps);
+
+/* Observables at the canonical centre (site 0 after a step).  Synchronises the
+ * stream and writes *out (host). */
+tt_status tt_measure(tt_rho* rho, const tt_mpo* mpo, tt_obs* out);
+
+/* Statistics of the last tt_tdvp_step call (host *out). */
+tt_status tt_stats_get(const tt_rho* rho, tt_stats* out);
+
+/* Current bond dimensions: writes N+1 ints (host) to dims. */
+tt_status tt_rho_bond_dims(const tt_rho* rho, int* dims, int n);
+
+/* ---- checkpoint (versioned little-endian binary: sector tables, FP64
+ *      blocks, beta, logscale) ---------------------------------------------- */
+tt_status tt_rho_save(tt_rho* rho, const char* path);
+tt_status tt_rho_load(tt_ctx* ctx, const tt_mpo* mpo, const char* path,
+                      const tt_run_opts* opts, tt_rho** out);
+
+/* ---- kernel-level entry points (one H_eff apply on given tensors) --------
+ *
+ * Bond k carries nsec[k] sectors; sector r of bond k has charge
+ * (qn[r], qs[r]) = (particle number, 2 Sz) and dimension qd[r], listed in
+ * strictly increasing (qn, qs) order.  Arrays for bonds are concatenated.
+ *
+ * Site tensor x (bond j -> bond j+1) layout: blocks (a_l sector l, pair sector
+ * p, a_r sector r) with charge(r) = charge(l) + p, ordered by r, then l, then
+ * p, with the nine pair charges p = charge(sigma) - charge(sigma') taken in
+ * increasing (n, 2Sz) order; each block row-major [a_l][pair][a_r], the pairs
+ * (sigma, sigma') of charge p in increasing 4 sigma + sigma'.
+ *
+ * Environment layout (bond k, MPO channels w = 0..tt_mpo_bond_dim(k)-1 with
+ * channel charge c_w from tt_mpo_channel_charge): per ket sector b in bond order, a
+ * row-major matrix of rows (w ascending, bra index a in sector b + c_w, only
+ * channels whose sector exists) and d_b columns; matrices concatenated.
+ *   L (bond j):   L[a, w, b] = sum over sites < j, bra a, ket b.
+ *   R (bond j+1): R[a, w, b] = sum over sites > j, bra a, ket b.
+ * tt_layout_sizes() returns the element counts of x, L, R.
+ * All of x, L, R, y are host FP64 arrays; y receives H^(1) x in x's layout.
+ */
+tt_status tt_mpo_channel_charge(const tt_mpo* mpo, int k, int w, int* qn, int* qs);
+tt_status tt_layout_sizes(const tt_mpo* mpo, int site, const int* nsec_lr /*2*/,
+                          const int* qn, const int* qs, const int* qd,
+                          int64_t* x_size, int64_t* l_size, int64_t* r_size);
+tt_status tt_heff_apply_host(tt_ctx* ctx, const tt_mpo* mpo, int site, int precision,
+                             const int* nsec_lr, const int* qn, const int* qs, const int* qd,
+                             const double* L, const double* R, const double* x, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TANTRG_H */

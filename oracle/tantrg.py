@@ -22,7 +22,8 @@ Readings taken where the paper is silent (also listed in the design doc):
 * QR gauge: sign convention diag(R) >= 0.
 * Growth truncation: keep at most D_max values, drop s <= svd_cut * s_max,
   never cut between s_k and s_{k+1} when s_k - s_{k+1} <= degen_tol * s_k +
-  1e-13 * s_max (a degenerate group is kept or dropped whole).
+  1e-14 * s_max (a degenerate group is kept or dropped whole).  svd_cut =
+  1e-12 keeps the decision two orders above the rounding noise of the SVD.
 * Norm tracking: after every exponential the centre tensor is normalised and
   ln(norm) is added to logscale.
 """
@@ -39,7 +40,7 @@ BREAKDOWN_TOL = 1e-13
 # Absolute guard of the degeneracy test, in units of the largest singular value:
 # exactly degenerate pairs (spin flip) come out of any SVD split by a few ulps
 # of s_max, which for small values exceeds a purely relative tolerance.
-DEGEN_ABS = 1e-13
+DEGEN_ABS = 1e-14
 
 
 # ----------------------------------------------------------------------------
@@ -205,23 +206,67 @@ def _normalise(st: State, x):
     return x / nu
 
 
-def init_state(W: list, beta0: float) -> State:
-    """rho_h(beta0) = I - beta0 H / 2 as an MPO of bond dimension D_H (main text,
-    "Benchmarks on noninteracting fermions": rho_0 = 1 - tau_0 H built from the
-    MPO of H), right-canonicalised by LQ from the right (Supplement,
-    "MPS/MPO manifold": canonical centre at site 0)."""
+def _right_canonicalise(st: State):
+    for j in range(st.N - 1, 0, -1):
+        Ar, S = lq_right(st.A[j])
+        st.A[j] = Ar
+        st.A[j - 1] = np.tensordot(st.A[j - 1], S, axes=([3], [0]))
+
+
+def init_state(W: list, beta0: float, compress_cut: float = 1e-14) -> State:
+    """rho_h(beta0) = I - beta0 H / 2 as an MPO built from the MPO of H (main
+    text, "Benchmarks on noninteracting fermions": rho_0 = 1 - tau_0 H with a
+    compact representation from the MPO of H, D = D_H), brought to its compact
+    form and right-canonicalised (canonical centre at site 0).
+
+    Compact form (a reading: the paper calls the representation compact but
+    does not fix it): right-canonicalise by LQ, then one left-to-right SVD
+    sweep that drops singular values s <= compress_cut * s_max of each bond,
+    then right-canonicalise again.  The bond spaces are then the operator
+    Schmidt spaces of rho_0, independent of how the MPO of H was written.
+    """
     N = len(W)
     A = [w.copy() for w in W]
     last = -0.5 * beta0 * W[N - 1].copy()
     last[0, :, :, 0] += np.eye(4)  # the "start" row closed with the identity
     A[N - 1] = last
     st = State(W=W, A=A)
-    for j in range(N - 1, 0, -1):
-        Ar, S = lq_right(st.A[j])
-        st.A[j] = Ar
-        st.A[j - 1] = np.tensordot(st.A[j - 1], S, axes=([3], [0]))
+    _right_canonicalise(st)
+    for j in range(N - 1):
+        Dl, _, _, Dr = st.A[j].shape
+        U, s, Vt = np.linalg.svd(st.A[j].reshape(Dl * 16, Dr), full_matrices=False)
+        k = int(np.count_nonzero(s > compress_cut * s[0]))
+        st.A[j] = U[:, :k].reshape(Dl, 4, 4, k)
+        st.A[j + 1] = np.tensordot(s[:k, None] * Vt[:k], st.A[j + 1], axes=([1], [0]))
+    _right_canonicalise(st)
     st.A[0] = _normalise(st, st.A[0])
     st.beta = beta0
+    build_envs(st)
+    return st
+
+
+def pad_to_full_rank(st: State) -> State:
+    """Embed the right-canonical state into bonds of the maximal dimension
+    min(16^k, 16^(N-k)) by orthonormal completion (zero weight).  With every
+    bond maximal the MPS manifold is the whole space, so 1-TDVP carries no
+    projection error (Supplement, "Splitting method": exact on the tangent
+    space); used to pin the integrator against exact diagonalisation."""
+    N = st.N
+    for j in range(N - 1, 0, -1):
+        A = st.A[j]
+        Dl, _, _, Dr = A.shape
+        full = min(16 ** j, 16 ** (N - j))
+        if Dl >= full:
+            continue
+        M = A.reshape(Dl, 16 * Dr)                  # orthonormal rows
+        Qc, _ = np.linalg.qr(np.concatenate([M.T, np.eye(16 * Dr)], axis=1))
+        P = Qc[:, :full].T                          # first Dl rows span M's rows
+        sign = np.sign(np.sum(P[:Dl] * M, axis=1))
+        P[:Dl] *= sign[:, None]
+        st.A[j] = P.reshape(full, 4, 4, Dr)
+        prev = st.A[j - 1]
+        pad = np.zeros(prev.shape[:3] + (full - Dl,))
+        st.A[j - 1] = np.concatenate([prev, pad], axis=3)
     build_envs(st)
     return st
 
@@ -295,7 +340,7 @@ def tdvp1_step(st: State, dtau: float, K: int = 8):
 @dataclass
 class TruncOpts:
     D_max: int
-    svd_cut: float = 1e-14
+    svd_cut: float = 1e-12
     degen_tol: float = 1e-10
 
 
@@ -415,11 +460,15 @@ def hermiticity_defect(st: State) -> float:
 # ----------------------------------------------------------------------------
 
 def run(W, beta0: float, dtau: float, beta_end: float, opts: TruncOpts, K: int = 8,
-        grow_until: float = 1.0, callback=None, max_grow_steps=None):
+        grow_until: float = 1.0, callback=None, max_grow_steps=None, pad_full: bool = False):
     """Growth with 2-TDVP until every bond is saturated or beta >= grow_until,
     then 1-TDVP steps until beta >= beta_end (the hybrid scheme of the main
-    text with a linear grid).  ``callback(st, stage)`` runs after every step."""
+    text with a linear grid).  ``callback(st, stage)`` runs after every step.
+    pad_full: start from the state padded to maximal bonds (no growth)."""
     st = init_state(W, beta0)
+    if pad_full:
+        pad_to_full_rank(st)
+        max_grow_steps = 0
     n_grow = 0
     eps = 1e-12
     while st.beta < beta_end - eps:

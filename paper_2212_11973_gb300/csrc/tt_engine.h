@@ -1,0 +1,135 @@
+// Internal engine types behind the C ABI (tantrg.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tantrg.h"
+#include "tt_core.h"
+#include "tt_kernels.h"
+#include "tt_plans.h"
+
+struct tt_ctx {
+  cudaStream_t st = nullptr;
+  tt_alloc_cb cb{};
+  bool has_cb = false;
+  std::string err;
+  cusolverDnHandle_t sol = nullptr;
+};
+
+struct tt_mpo {
+  tt_ctx* ctx = nullptr;
+  tt::ModelSpec spec{};
+  tt::Mpo mpo;
+  tt::LocalSpace ls2;  // two-site product space (growth)
+};
+
+namespace tt {
+
+struct Err {
+  tt_status st;
+  std::string msg;
+};
+
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+void* dalloc(tt_ctx* c, size_t bytes);
+void dfree(tt_ctx* c, DBuf& b);
+void ensure(tt_ctx* c, DBuf& b, size_t bytes);  // grow-only, contents not kept
+void check_cuda(cudaError_t e, const char* what);
+
+struct DevGemmBuf {
+  DevGemm d;
+  DBuf buf;
+  GemmPlan host;       // kept for the bounds check before the first launch
+  bool checked = false;
+};
+struct DevGatherBuf {
+  DevGather d;
+  DBuf buf;
+  GatherPlan host;
+  bool checked = false;
+};
+struct DevCopyBuf {
+  DevCopy d;
+  DBuf buf;
+  CopyPlan host;
+  bool checked = false;
+};
+
+// Element capacity of every slot (per split level for split-BF16 slots);
+// -1 = slot unused.  Plans are checked against it on the host before their
+// first launch so that an indexing error raises instead of faulting the GPU.
+struct Caps {
+  int64_t n[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+};
+void check_plan(const GemmPlan& p, const Caps& c, const char* what);
+void check_plan(const GatherPlan& p, const Caps& c, const char* what);
+void check_plan(const CopyPlan& p, const Caps& c, const char* what);
+
+void upload(tt_ctx* c, const GemmPlan& p, DevGemmBuf& o);
+void upload(tt_ctx* c, const GatherPlan& p, DevGatherBuf& o);
+void upload(tt_ctx* c, const CopyPlan& p, DevCopyBuf& o);
+void release(tt_ctx* c, DevGemmBuf& o);
+void release(tt_ctx* c, DevGatherBuf& o);
+void release(tt_ctx* c, DevCopyBuf& o);
+
+struct SiteDev {
+  bool valid = false;
+  SitePlanHost h;
+  DevGemmBuf s1, s3, s3l, r1, r3;
+  DevGatherBuf s2, r2;
+};
+struct BondDev {
+  bool valid = false;
+  BondPlanHost h;
+  DevGemmBuf b1, b2;
+};
+struct QrDev {
+  bool valid = false;
+  QrPlanHost h;
+  DBuf jobs;
+  DevCopyBuf gather, scatter, rout;
+};
+struct MeasDev {
+  bool valid = false;
+  DevGemmBuf t, el;
+  DBuf items;
+  int nitems = 0;
+  BondMatLayout next;
+};
+
+}  // namespace tt
+
+struct tt_rho {
+  tt_ctx* ctx = nullptr;
+  const tt_mpo* mpo = nullptr;
+  tt_run_opts opts{};
+  int N = 0;
+  int nsplit = 0;  // 0 = FP64
+  bool poisoned = false;
+  double beta = 0.0;
+  std::vector<tt::Bond> bond;           // N + 1
+  std::vector<tt::SiteLayout> lay;      // N
+  std::vector<tt::DBuf> A;              // N site tensors (FP64)
+  std::vector<tt::DBuf> L, R, Lsp, Rsp; // environments (FP64) and split copies
+  std::vector<int64_t> Lsize, Rsize;
+  std::vector<tt::SiteDev> sp;
+  std::vector<tt::BondDev> bp;
+  std::vector<tt::QrDev> qrl, lqr;
+  std::vector<tt::DevGemmBuf> absl, absr;
+  std::vector<char> absl_ok, absr_ok;
+  std::vector<tt::MeasDev> meas;
+  tt::DBuf Qk, W, Xs, T1, T2, Sb, ws, partial, ks, rs, tmp, obs, el0, el1;
+  int64_t ldq = 0;
+  tt_stats stats{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool stats_pending = false;
+  double heff_flops_acc = 0, step_flops_acc = 0;
+  long long launches_acc = 0;
+};

@@ -1,0 +1,895 @@
+// Device kernels of the tanTRG hot path (sm_103a).
+//
+//  * grouped, segmented GEMM (FP64 FMA; split-BF16 x3 on the tensor cores):
+//    every contraction of the H_eff apply (Supplement, Fig. "Lanczos": L_i A_i,
+//    then H_i, then R_i), the bond apply (Fig. "optimalB"(d)), the environment
+//    updates and the absorb step is a list of groups C_g = sum_seg A_seg B_seg;
+//  * W gather: applies the sparse MPO tensor between the two GEMM stages;
+//  * Lanczos vector kernels in FP64 (Supplement, "Lanczos-based exponential
+//    method"), with deterministic two-stage reductions;
+//  * the small Krylov exponential exp(t T) e_1 by cyclic Jacobi (Golub & Van
+//    Loan, Sec. 8.5) and CUDA's exp();
+//  * Householder QR (FP64) of the per-sector gauge matrices.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "tt_kernels.h"
+
+namespace tt {
+
+namespace {
+
+__device__ __forceinline__ int slot_of(Ref r) { return (int)(r >> 56); }
+__device__ __forceinline__ long long off_of(Ref r) { return (long long)(r & 0x00FFFFFFFFFFFFFFull); }
+
+template <typename T>
+__device__ __forceinline__ T* rptr(const Bases& b, Ref r) {
+  return reinterpret_cast<T*>(b.p[slot_of(r)]) + off_of(r);
+}
+
+constexpr int NBLK = 304;  // 2 x 152 SMs for the vector reductions
+constexpr int VT = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 grouped GEMM: one 64 x 64 output tile per CTA, 256 threads, 4 x 4 per
+// thread, K staged through shared memory in chunks of 16.
+// ---------------------------------------------------------------------------
+constexpr int FBM = 64, FBN = 64, FBK = 16;
+
+__global__ void __launch_bounds__(256) gemm_f64_kernel(const GGroup* __restrict__ groups,
+                                                       const GSeg* __restrict__ segs,
+                                                       const GTile* __restrict__ tiles, Bases bs) {
+  __shared__ double As[FBK][FBM + 1];
+  __shared__ double Bs[FBK][FBN + 1];
+  const GTile tl = tiles[blockIdx.x];
+  const GGroup g = groups[tl.g];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;  // 16 x 16 threads, each 4 x 4 outputs
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int si = g.seg0; si < g.seg1; ++si) {
+    const GSeg sg = segs[si];
+    const double* A = rptr<const double>(bs, sg.A);
+    const double* B = rptr<const double>(bs, sg.B);
+    for (int k0 = 0; k0 < sg.K; k0 += FBK) {
+      // load A tile: FBM x FBK logical (m, k)
+      for (int e = tid; e < FBM * FBK; e += 256) {
+        int mm, kk;
+        if (sg.tA) { mm = e % FBM; kk = e / FBM; } else { kk = e % FBK; mm = e / FBK; }
+        int gm = tl.m0 + mm, gk = k0 + kk;
+        double v = 0.0;
+        if (gm < g.M && gk < sg.K)
+          v = sg.tA ? A[(long long)gk * sg.lda + gm] : A[(long long)gm * sg.lda + gk];
+        As[kk][mm] = v;
+      }
+      for (int e = tid; e < FBN * FBK; e += 256) {
+        int nn, kk;
+        if (sg.tB) { kk = e % FBK; nn = e / FBK; } else { nn = e % FBN; kk = e / FBN; }
+        int gn = tl.n0 + nn, gk = k0 + kk;
+        double v = 0.0;
+        if (gn < g.N && gk < sg.K)
+          v = sg.tB ? B[(long long)gn * sg.ldb + gk] : B[(long long)gk * sg.ldb + gn];
+        Bs[kk][nn] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < FBK; ++kk) {
+        double a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+  }
+  double* C = rptr<double>(bs, g.C);
+  const bool accum = g.flags & 1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int gm = tl.m0 + ty + 16 * i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gn = tl.n0 + tx + 16 * j;
+      if (gn >= g.N) continue;
+      double* c = C + (long long)gm * g.ldc + gn;
+      *c = accum ? *c + acc[i][j] : acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Split-BF16 grouped GEMM on the tensor cores (mma.sync m16n8k16, FP32
+// accumulation).  Operands are stored as NS bf16 levels x = x0 + x1 (+ x2),
+// level l at element offset l * lo[slot]; the products with l_A + l_B < NS are
+// summed: NS = 2 -> 3 products (~2^-16 relative), NS = 3 -> 6 products
+// (~2^-24).  The FP32 accumulators of every 32-wide K chunk are folded into a
+// two-float (hi, lo) sum with TwoSum (Knuth, TAOCP vol. 2, 4.2.2), so the
+// accumulation error does not grow with K.  64 x 64 tile per CTA, 4 warps of
+// 32 x 32.  Output FP64 or FP32 (flags bit1).
+// ---------------------------------------------------------------------------
+constexpr int HBM = 64, HBN = 64, HBK = 32, HPAD = 8;
+
+__device__ __forceinline__ void mma_bf16_16816(float* c, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float ap = s - bp;
+  lo += (hi - ap) + (x - bp);
+  hi = s;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(128) gemm_bf16_split_kernel(const GGroup* __restrict__ groups,
+                                                              const GSeg* __restrict__ segs,
+                                                              const GTile* __restrict__ tiles, Bases bs) {
+  __shared__ __align__(16) __nv_bfloat16 As[NS][HBM][HBK + HPAD];
+  __shared__ __align__(16) __nv_bfloat16 Bs[NS][HBN][HBK + HPAD];
+  const GTile tl = tiles[blockIdx.x];
+  const GGroup g = groups[tl.g];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int gid = lane >> 2, tig = lane & 3;
+  float acc[2][4][4], hi[2][4][4], lo[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) { acc[i][j][r] = 0.f; hi[i][j][r] = 0.f; lo[i][j][r] = 0.f; }
+
+  for (int si = g.seg0; si < g.seg1; ++si) {
+    const GSeg sg = segs[si];
+    const __nv_bfloat16* A0 = rptr<const __nv_bfloat16>(bs, sg.A);
+    const __nv_bfloat16* B0 = rptr<const __nv_bfloat16>(bs, sg.B);
+    const long long loA = bs.lo[slot_of(sg.A)], loB = bs.lo[slot_of(sg.B)];
+    for (int k0 = 0; k0 < sg.K; k0 += HBK) {
+      for (int e = tid; e < HBM * HBK; e += 128) {
+        int mm, kk;
+        if (sg.tA) { mm = e % HBM; kk = e / HBM; } else { kk = e % HBK; mm = e / HBK; }
+        const int gm = tl.m0 + mm, gk = k0 + kk;
+        const bool in = gm < g.M && gk < sg.K;
+        const long long o = sg.tA ? (long long)gk * sg.lda + gm : (long long)gm * sg.lda + gk;
+#pragma unroll
+        for (int l = 0; l < NS; ++l) As[l][mm][kk] = in ? A0[l * loA + o] : __float2bfloat16(0.f);
+      }
+      for (int e = tid; e < HBN * HBK; e += 128) {
+        int nn, kk;
+        if (sg.tB) { kk = e % HBK; nn = e / HBK; } else { nn = e % HBN; kk = e / HBN; }
+        const int gn = tl.n0 + nn, gk = k0 + kk;
+        const bool in = gn < g.N && gk < sg.K;
+        const long long o = sg.tB ? (long long)gn * sg.ldb + gk : (long long)gk * sg.ldb + gn;
+#pragma unroll
+        for (int l = 0; l < NS; ++l) Bs[l][nn][kk] = in ? B0[l * loB + o] : __float2bfloat16(0.f);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int pass = 0; pass < (NS == 2 ? 3 : 6); ++pass) {
+        // (la, lb): NS=2: (0,0) (0,1) (1,0); NS=3 adds (0,2) (1,1) (2,0); small products first
+        const int order = (NS == 2 ? 2 : 5) - pass;
+        const int la = (order == 2 || order == 4) ? 1 : (order == 5 ? 2 : 0);
+        const int lb = (order == 1 || order == 4) ? 1 : (order == 3 ? 2 : 0);
+#pragma unroll
+        for (int ks = 0; ks < HBK; ks += 16) {
+          uint32_t af[2][4], bf[4][2];
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            const int r0 = wm + 16 * i + gid;
+            af[i][0] = *reinterpret_cast<const uint32_t*>(&As[la][r0][ks + 2 * tig]);
+            af[i][1] = *reinterpret_cast<const uint32_t*>(&As[la][r0 + 8][ks + 2 * tig]);
+            af[i][2] = *reinterpret_cast<const uint32_t*>(&As[la][r0][ks + 8 + 2 * tig]);
+            af[i][3] = *reinterpret_cast<const uint32_t*>(&As[la][r0 + 8][ks + 8 + 2 * tig]);
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int c0 = wn + 8 * j + gid;
+            bf[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[lb][c0][ks + 2 * tig]);
+            bf[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[lb][c0][ks + 8 + 2 * tig]);
+          }
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bf[j]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            two_sum_acc(hi[i][j][r], lo[i][j][r], acc[i][j][r]);
+            acc[i][j][r] = 0.f;
+          }
+    }
+  }
+  const bool accum = g.flags & 1;
+  const bool out_f32 = g.flags & 2;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int gm = tl.m0 + wm + 16 * i + gid + ((r >= 2) ? 8 : 0);
+        const int gn = tl.n0 + wn + 8 * j + 2 * tig + (r & 1);
+        if (gm >= g.M || gn >= g.N) continue;
+        const long long o = (long long)gm * g.ldc + gn;
+        const double v = (double)hi[i][j][r] + (double)lo[i][j][r];
+        if (out_f32) {
+          float* C = rptr<float>(bs, g.C) + o;
+          *C = accum ? *C + (float)v : (float)v;
+        } else {
+          double* C = rptr<double>(bs, g.C) + o;
+          *C = accum ? *C + v : v;
+        }
+      }
+}
+
+// ---------------------------------------------------------------------------
+// W gather: dst[r, c] = sum_k coef_k src_k[r, c]  (one CTA per item).
+// ---------------------------------------------------------------------------
+template <int IN, int OUT>
+__global__ void __launch_bounds__(256) gather_kernel(const GItem* __restrict__ items,
+                                                     const GContrib* __restrict__ cs, Bases bs) {
+  const GItem it = items[blockIdx.x];
+  const long long total = (long long)it.rows * it.cols;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+    const int r = (int)(e / it.cols), c = (int)(e % it.cols);
+    double acc = 0.0;
+    for (int k = it.c0; k < it.c1; ++k) {
+      const GContrib cb = cs[k];
+      const long long so = (long long)r * cb.src_rs + c;
+      double v;
+      if (IN == 0) v = rptr<const double>(bs, cb.src)[so];
+      else v = (double)rptr<const float>(bs, cb.src)[so];
+      acc = fma(cb.coef, v, acc);
+    }
+    const long long d = (long long)r * it.dst_rs + c;
+    if (OUT == 0) {
+      rptr<double>(bs, it.dst)[d] = acc;
+    } else if (OUT == 1) {
+      rptr<float>(bs, it.dst)[d] = (float)acc;
+    } else {
+      // OUT = 2 / 3: split into OUT bf16 levels
+      __nv_bfloat16* p = rptr<__nv_bfloat16>(bs, it.dst) + d;
+      const long long lo = bs.lo[slot_of(it.dst)];
+      double rem = acc;
+#pragma unroll
+      for (int l = 0; l < OUT; ++l) {
+        __nv_bfloat16 h = __double2bfloat16(rem);
+        p[l * lo] = h;
+        rem -= (double)__bfloat162float(h);
+      }
+    }
+  }
+}
+
+// Strided 2D copy, FP64.
+__global__ void __launch_bounds__(256) copy_kernel(const CItem* __restrict__ items, Bases bs) {
+  const CItem it = items[blockIdx.x];
+  const double* src = rptr<const double>(bs, it.src);
+  double* dst = rptr<double>(bs, it.dst);
+  const long long total = (long long)it.rows * it.cols;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+    long long r, c;
+    if (it.dst_cs == 1) { r = e / it.cols; c = e % it.cols; } else { c = e / it.rows; r = e % it.rows; }
+    dst[r * it.dst_rs + c * it.dst_cs] = src[r * it.src_rs + c * it.src_cs];
+  }
+}
+
+// x (FP64, n) -> ns bf16 levels out[l * n + i], x ~ sum_l out[l]
+__global__ void split_bf16_kernel(const double* __restrict__ x, long long n, int ns, __nv_bfloat16* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double rem = x[i];
+    for (int l = 0; l < ns; ++l) {
+      __nv_bfloat16 h = __double2bfloat16(rem);
+      out[l * n + i] = h;
+      rem -= (double)__bfloat162float(h);
+    }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Lanczos vector kernels
+// ---------------------------------------------------------------------------
+// partial[blk * 17 + j] = sum over this block's chunk of Q_j . w   (j < nv)
+template <int MAXV>
+__global__ void __launch_bounds__(VT) multidot_kernel(const double* __restrict__ Q, long long ldq, int j0, int nv,
+                                                      const double* __restrict__ w, long long n,
+                                                      double* __restrict__ partial) {
+  double acc[MAXV];
+#pragma unroll
+  for (int j = 0; j < MAXV; ++j) acc[j] = 0.0;
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
+    double wi = w[i];
+#pragma unroll
+    for (int j = 0; j < MAXV; ++j)
+      if (j < nv) acc[j] = fma(Q[(long long)(j0 + j) * ldq + i], wi, acc[j]);
+  }
+  __shared__ double red[VT / 32][MAXV];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < MAXV; ++j) {
+    double v = warp_sum(acc[j]);
+    if (lane == 0) red[wp][j] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    double s = 0.0;
+    for (int q = 0; q < VT / 32; ++q) s += red[q][threadIdx.x];
+    partial[blockIdx.x * 17 + threadIdx.x] = s;
+  }
+}
+
+__global__ void sumsq_kernel(const double* __restrict__ v, long long n, double* __restrict__ partial) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+    acc = fma(v[i], v[i], acc);
+  __shared__ double red[VT / 32];
+  double s = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < VT / 32; ++q) t += red[q];
+    partial[blockIdx.x * 17] = t;
+  }
+}
+
+// out[j] = sum_b partial[b * 17 + j] in a fixed order (deterministic)
+__device__ void finalize_sums(const double* partial, int nblk, int nv, double* out) {
+  // called by one warp
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < nv; ++j) {
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += partial[b * 17 + j];
+    s = warp_sum(s);
+    if (lane == 0) out[j] = s;
+  }
+}
+
+__global__ void norm_init_finalize(const double* partial, int nblk, KrylovState* ks) {
+  __shared__ double s;
+  finalize_sums(partial, nblk, 1, &s);
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    double nb = sqrt(s);
+    ks->nb = nb;
+    ks->hscale = 0.0;
+    ks->resid = 0.0;
+    ks->kdim = 0;
+    ks->broken = 0;
+    ks->bad = !isfinite(nb) ? 1 : 0;
+    for (int j = 0; j < 17; ++j) { ks->alpha[j] = 0; ks->beta[j] = 0; ks->h[j] = 0; ks->c[j] = 0; }
+  }
+}
+
+__global__ void scale_kernel(const double* __restrict__ v, long long n, const double* __restrict__ denom,
+                             const int* __restrict__ dead, double* __restrict__ out) {
+  const double d = *denom;
+  const bool z = (dead && *dead) || d == 0.0;
+  const double inv = z ? 0.0 : 1.0 / d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = v[i] * inv;
+}
+
+__global__ void alpha_finalize(const double* partial, int nblk, int k, KrylovState* ks) {
+  __shared__ double s;
+  finalize_sums(partial, nblk, 1, &s);
+  __syncwarp();
+  if (threadIdx.x == 0 && !ks->broken) ks->alpha[k] = s;
+}
+
+__global__ void three_term_kernel(const double* __restrict__ Q, long long ldq, int k, double* __restrict__ w,
+                                  long long n, const KrylovState* __restrict__ ks) {
+  const double a = ks->alpha[k];
+  const double b = (k > 0) ? ks->beta[k - 1] : 0.0;
+  const double* qk = Q + (long long)k * ldq;
+  const double* qp = Q + (long long)(k > 0 ? k - 1 : 0) * ldq;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double v = w[i] - a * qk[i];
+    if (k > 0) v -= b * qp[i];
+    w[i] = v;
+  }
+}
+
+__global__ void h_finalize(const double* partial, int nblk, int nv, KrylovState* ks) {
+  finalize_sums(partial, nblk, nv, ks->h);
+}
+
+// w -= sum_j h_j Q_j ; optional partial ||w||^2
+__global__ void __launch_bounds__(VT) axpy_multi_kernel(const double* __restrict__ Q, long long ldq, int nv,
+                                                        const KrylovState* __restrict__ ks, double* __restrict__ w,
+                                                        long long n, double* __restrict__ partial) {
+  __shared__ double h[17];
+  if (threadIdx.x < 17) h[threadIdx.x] = ks->h[threadIdx.x];
+  __syncthreads();
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
+    double v = w[i];
+    for (int j = 0; j < nv; ++j) v -= h[j] * Q[(long long)j * ldq + i];
+    w[i] = v;
+    acc = fma(v, v, acc);
+  }
+  if (partial) {
+    __shared__ double red[VT / 32];
+    double s = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < VT / 32; ++q) t += red[q];
+      partial[blockIdx.x * 17] = t;
+    }
+  }
+}
+
+// beta_k = ||w||; breakdown test of the oracle; stores beta (or 0 if broken).
+__global__ void beta_finalize(const double* partial, int nblk, int k, int K, double tol, KrylovState* ks) {
+  __shared__ double s;
+  finalize_sums(partial, nblk, 1, &s);
+  __syncwarp();
+  if (threadIdx.x != 0) return;
+  if (ks->broken) {
+    ks->beta[k] = 0.0;
+    return;
+  }
+  double b = sqrt(s);
+  if (!isfinite(b) || !isfinite(ks->alpha[k])) ks->bad = 1;
+  double hs = fmax(ks->hscale, fabs(ks->alpha[k]) + b);
+  ks->hscale = hs;
+  ks->kdim = k + 1;
+  if (k == K - 1) {
+    ks->beta[k] = b;  // residual norm, not part of T
+    return;
+  }
+  if (b <= tol * hs) {
+    ks->broken = 1;
+    ks->beta[k] = 0.0;
+    return;
+  }
+  ks->beta[k] = b;
+}
+
+// exp(t T) e_1 for the kdim x kdim tridiagonal T (cyclic Jacobi eigensolver).
+__global__ void krylov_exp_kernel(KrylovState* ks, double t, int K) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int m = ks->kdim;
+  double A[16][16], V[16][16];
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      A[i][j] = 0.0;
+      V[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+  for (int i = 0; i < m; ++i) A[i][i] = ks->alpha[i];
+  for (int i = 0; i + 1 < m; ++i) A[i][i + 1] = A[i + 1][i] = ks->beta[i];
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        if (i == j) diag += A[i][i] * A[i][i];
+        else off += A[i][j] * A[i][j];
+      }
+    if (off <= 1e-32 * diag || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        double apq = A[p][q];
+        if (apq == 0.0) continue;
+        double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+        double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+        double c = 1.0 / sqrt(1.0 + tt * tt), s = tt * c;
+        for (int k = 0; k < m; ++k) {  // A <- A J
+          double akp = A[k][p], akq = A[k][q];
+          A[k][p] = c * akp - s * akq;
+          A[k][q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // A <- J^T A
+          double apk = A[p][k], aqk = A[q][k];
+          A[p][k] = c * apk - s * aqk;
+          A[q][k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < 17; ++i) ks->c[i] = 0.0;
+  for (int i = 0; i < m; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < m; ++j) s += V[i][j] * exp(t * A[j][j]) * V[0][j];
+    ks->c[i] = s;
+  }
+  ks->resid = (!ks->broken && m == K) ? ks->nb * ks->beta[K - 1] * fabs(ks->c[K - 1]) : 0.0;
+}
+
+__global__ void __launch_bounds__(VT) combine_kernel(const double* __restrict__ Q, long long ldq,
+                                                     const KrylovState* __restrict__ ks, double* __restrict__ y,
+                                                     long long n, double* __restrict__ partial) {
+  __shared__ double c[17];
+  __shared__ int m;
+  if (threadIdx.x < 17) c[threadIdx.x] = ks->c[threadIdx.x] * ks->nb;
+  if (threadIdx.x == 0) m = ks->kdim;
+  __syncthreads();
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT) {
+    double v = 0.0;
+    for (int j = 0; j < m; ++j) v = fma(c[j], Q[(long long)j * ldq + i], v);
+    y[i] = v;
+    acc = fma(v, v, acc);
+  }
+  __shared__ double red[VT / 32];
+  double s = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < VT / 32; ++q) t += red[q];
+    partial[blockIdx.x * 17] = t;
+  }
+}
+
+__global__ void nrm_finalize(const double* partial, int nblk, KrylovState* ks, RhoScalars* rs) {
+  __shared__ double s;
+  finalize_sums(partial, nblk, 1, &s);
+  __syncwarp();
+  if (threadIdx.x != 0) return;
+  double nrm = sqrt(s);
+  ks->nrm = nrm;
+  if (!isfinite(nrm) || nrm == 0.0 || ks->bad) {
+    rs->bad = 1;
+    return;
+  }
+  rs->logscale += log(nrm);
+  rs->resid_max = fmax(rs->resid_max, ks->resid);
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR, one CTA per column-major matrix (ld = m).
+// ---------------------------------------------------------------------------
+constexpr int QRT = 256;
+constexpr int QR_MAXN = 2048;
+
+__global__ void __launch_bounds__(QRT) qr_kernel(const QrJob* __restrict__ jobs, double* __restrict__ ws) {
+  const QrJob J = jobs[blockIdx.x];
+  const int m = J.m, n = J.n;
+  double* A = ws + J.a;
+  double* Qm = ws + J.q;
+  double* R = ws + J.r;
+  __shared__ double tau_s[QR_MAXN];
+  __shared__ double red[QRT / 32];
+  __shared__ double bcast;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = QRT / 32;
+  const int kmax = m < n ? m : n;
+  for (int k = 0; k < kmax; ++k) {
+    double* col = A + (long long)k * m;
+    double s = 0.0;
+    for (int i = k + 1 + threadIdx.x; i < m; i += QRT) s = fma(col[i], col[i], s);
+    s = warp_sum(s);
+    if (lane == 0) red[wp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < nw; ++q) t += red[q];
+      double alpha = col[k];
+      double tau = 0.0, scale = 0.0;
+      if (t > 0.0) {
+        double beta = -copysign(sqrt(alpha * alpha + t), alpha);
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+        col[k] = beta;
+      }
+      tau_s[k] = tau;
+      bcast = scale;
+    }
+    __syncthreads();
+    const double scale = bcast;
+    if (tau_s[k] != 0.0)
+      for (int i = k + 1 + threadIdx.x; i < m; i += QRT) col[i] *= scale;
+    __syncthreads();
+    const double tau = tau_s[k];
+    if (tau != 0.0) {
+      for (int j = k + 1 + wp; j < n; j += nw) {
+        double* cj = A + (long long)j * m;
+        double w = 0.0;
+        for (int i = k + 1 + lane; i < m; i += 32) w = fma(col[i], cj[i], w);
+        w = warp_sum(w) + cj[k];
+        w *= tau;
+        if (lane == 0) cj[k] -= w;
+        for (int i = k + 1 + lane; i < m; i += 32) cj[i] = fma(-w, col[i], cj[i]);
+      }
+    }
+    __syncthreads();
+  }
+  // R (n x n, column-major)
+  for (long long e = threadIdx.x; e < (long long)n * n; e += QRT) {
+    int i = (int)(e % n), j = (int)(e / n);
+    R[e] = (i <= j && i < m) ? A[(long long)j * m + i] : 0.0;
+  }
+  // Q = H_0 ... H_{kmax-1} [I_n ; 0]   (columns j >= m stay zero)
+  for (long long e = threadIdx.x; e < (long long)m * n; e += QRT) {
+    int i = (int)(e % m), j = (int)(e / m);
+    Qm[e] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int k = kmax - 1; k >= 0; --k) {
+    const double tau = tau_s[k];
+    if (tau == 0.0) continue;
+    const double* v = A + (long long)k * m;
+    for (int j = k + wp; j < n; j += nw) {
+      double* qj = Qm + (long long)j * m;
+      double w = 0.0;
+      for (int i = k + 1 + lane; i < m; i += 32) w = fma(v[i], qj[i], w);
+      w = warp_sum(w) + qj[k];
+      w *= tau;
+      if (lane == 0) qj[k] -= w;
+      for (int i = k + 1 + lane; i < m; i += 32) qj[i] = fma(-w, v[i], qj[i]);
+    }
+    __syncthreads();
+  }
+  // sign convention diag(R) >= 0
+  for (int k = wp; k < n; k += nw) {
+    double d = (R[(long long)k * n + k] < 0.0) ? -1.0 : 1.0;
+    __syncwarp();
+    if (d < 0) {
+      for (int i = lane; i < m; i += 32) Qm[(long long)k * m + i] = -Qm[(long long)k * m + i];
+      for (int j = k + lane; j < n; j += 32) R[(long long)j * n + k] = -R[(long long)j * n + k];
+    }
+  }
+}
+
+__global__ void dot_finalize(const double* partial, int nblk, double* out) {
+  __shared__ double s;
+  finalize_sums(partial, nblk, 1, &s);
+  __syncwarp();
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void __launch_bounds__(VT) dot_kernel(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                                                 double* __restrict__ partial) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)VT + threadIdx.x; i < n; i += (long long)gridDim.x * VT)
+    acc = fma(x[i], y[i], acc);
+  __shared__ double red[VT / 32];
+  double s = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < VT / 32; ++q) t += red[q];
+    partial[blockIdx.x * 17] = t;
+  }
+}
+
+// Local observables at one site: partial[b*2 + {0,1}] = sum over block b of
+// A[a, pair, c] T[a, pair, c] w{n,d}(pair)  (T = EL A, right environment = 1).
+__global__ void __launch_bounds__(256) local_obs_kernel(const ObsItem* __restrict__ items, const double* __restrict__ A,
+                                                        const double* __restrict__ T, double* __restrict__ partial) {
+  const ObsItem it = items[blockIdx.x];
+  double sn = 0.0, sd = 0.0;
+  const long long total = (long long)it.dl * it.m * it.dr;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+    const int pr = (int)((e / it.dr) % it.m);
+    const double v = A[it.off + e] * T[it.off + e];
+    sn = fma(v, it.wn[pr], sn);
+    sd = fma(v, it.wd[pr], sd);
+  }
+  __shared__ double red[2][8];
+  sn = warp_sum(sn);
+  sd = warp_sum(sd);
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = sn; red[1][threadIdx.x >> 5] = sd; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int q = 0; q < 8; ++q) { a += red[0][q]; b += red[1][q]; }
+    partial[blockIdx.x * 2] = a;
+    partial[blockIdx.x * 2 + 1] = b;
+  }
+}
+
+__global__ void local_obs_finalize(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double a = 0, b = 0;
+  for (int i = 0; i < n; ++i) { a += partial[2 * i]; b += partial[2 * i + 1]; }
+  out[0] += a;
+  out[1] += b;
+}
+
+// rows of a column-major m x k matrix (ld) scaled by s[row]  /  columns scaled by s[col]
+__global__ void scale_rc_kernel(double* __restrict__ a, long long ld, int rows, int cols, const double* __restrict__ s,
+                                int by_col) {
+  const long long total = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e % rows), c = (int)(e / rows);
+    a[r + c * ld] *= by_col ? s[c] : s[r];
+  }
+}
+
+inline int grid_for(long long n) {
+  long long g = (n + VT - 1) / VT;
+  if (g > NBLK) g = NBLK;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+int lanczos_nblk() { return NBLK; }
+
+cudaError_t launch_gemm_f64(const DevGemm& g, const Bases& b, cudaStream_t s) {
+  if (g.ntiles64 == 0) return cudaSuccess;
+  gemm_f64_kernel<<<g.ntiles64, 256, 0, s>>>(g.groups, g.segs, g.tiles64, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_bf16(const DevGemm& g, const Bases& b, int nsplit, cudaStream_t s) {
+  if (g.ntiles64 == 0) return cudaSuccess;
+  if (nsplit == 2) gemm_bf16_split_kernel<2><<<g.ntiles64, 128, 0, s>>>(g.groups, g.segs, g.tiles64, b);
+  else if (nsplit == 3) gemm_bf16_split_kernel<3><<<g.ntiles64, 128, 0, s>>>(g.groups, g.segs, g.tiles64, b);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const DevGather& g, const Bases& b, int in_type, int out_type, cudaStream_t s) {
+  if (g.nitems == 0) return cudaSuccess;
+  if (in_type == 0 && out_type == 0) gather_kernel<0, 0><<<g.nitems, 256, 0, s>>>(g.items, g.contribs, b);
+  else if (in_type == 1 && out_type == 2) gather_kernel<1, 2><<<g.nitems, 256, 0, s>>>(g.items, g.contribs, b);
+  else if (in_type == 1 && out_type == 3) gather_kernel<1, 3><<<g.nitems, 256, 0, s>>>(g.items, g.contribs, b);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const DevCopy& c, const Bases& b, cudaStream_t s) {
+  if (c.nitems == 0) return cudaSuccess;
+  copy_kernel<<<c.nitems, 256, 0, s>>>(c.items, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_bf16(const double* x, int64_t n, int nsplit, void* out, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  split_bf16_kernel<<<grid_for(n) * 2, VT, 0, s>>>(x, n, nsplit, reinterpret_cast<__nv_bfloat16*>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) { return cudaMemsetAsync(p, 0, bytes, s); }
+
+cudaError_t k_norm_init(const double* v, int64_t n, double* partial, KrylovState* ks, double* q0, cudaStream_t s) {
+  int g = grid_for(n);
+  sumsq_kernel<<<g, VT, 0, s>>>(v, n, partial);
+  norm_init_finalize<<<1, 32, 0, s>>>(partial, g, ks);
+  scale_kernel<<<g, VT, 0, s>>>(v, n, &ks->nb, nullptr, q0);
+  return cudaGetLastError();
+}
+
+cudaError_t k_dots_alpha(const double* Q, int64_t ldq, int k, const double* w, int64_t n, double* partial,
+                         KrylovState* ks, cudaStream_t s) {
+  int g = grid_for(n);
+  multidot_kernel<1><<<g, VT, 0, s>>>(Q, ldq, k, 1, w, n, partial);
+  alpha_finalize<<<1, 32, 0, s>>>(partial, g, k, ks);
+  return cudaGetLastError();
+}
+
+cudaError_t k_three_term(const double* Q, int64_t ldq, int k, double* w, int64_t n, KrylovState* ks, cudaStream_t s) {
+  three_term_kernel<<<grid_for(n), VT, 0, s>>>(Q, ldq, k, w, n, ks);
+  return cudaGetLastError();
+}
+
+cudaError_t k_cgs_pass(const double* Q, int64_t ldq, int k, double* w, int64_t n, double* partial, KrylovState* ks,
+                       int last, double tol, int K, double* qnext, cudaStream_t s) {
+  int g = grid_for(n);
+  int nv = k + 1;
+  if (nv <= 4) multidot_kernel<4><<<g, VT, 0, s>>>(Q, ldq, 0, nv, w, n, partial);
+  else if (nv <= 8) multidot_kernel<8><<<g, VT, 0, s>>>(Q, ldq, 0, nv, w, n, partial);
+  else multidot_kernel<17><<<g, VT, 0, s>>>(Q, ldq, 0, nv, w, n, partial);
+  h_finalize<<<1, 32, 0, s>>>(partial, g, nv, ks);
+  axpy_multi_kernel<<<g, VT, 0, s>>>(Q, ldq, nv, ks, w, n, last ? partial : nullptr);
+  if (last) {
+    beta_finalize<<<1, 32, 0, s>>>(partial, g, k, K, tol, ks);
+    if (k < K - 1) scale_kernel<<<g, VT, 0, s>>>(w, n, &ks->beta[k], &ks->broken, qnext);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t k_krylov_exp(KrylovState* ks, double t, int K, cudaStream_t s) {
+  krylov_exp_kernel<<<1, 32, 0, s>>>(ks, t, K);
+  return cudaGetLastError();
+}
+
+cudaError_t k_combine(const double* Q, int64_t ldq, const KrylovState* ks, double* y, int64_t n, double* partial,
+                      KrylovState* ksw, cudaStream_t s) {
+  (void)ksw;
+  combine_kernel<<<grid_for(n), VT, 0, s>>>(Q, ldq, ks, y, n, partial);
+  return cudaGetLastError();
+}
+
+cudaError_t k_dot_plain(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t s) {
+  int g = grid_for(n);
+  dot_kernel<<<g, VT, 0, s>>>(x, y, n, partial);
+  dot_finalize<<<1, 32, 0, s>>>(partial, g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local_obs(const ObsItem* items, int nitems, const double* A, const double* T, double* partial,
+                             double* out, cudaStream_t s) {
+  if (nitems == 0) return cudaSuccess;
+  local_obs_kernel<<<nitems, 256, 0, s>>>(items, A, T, partial);
+  local_obs_finalize<<<1, 32, 0, s>>>(partial, nitems, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_rc(double* a, long long ld, int rows, int cols, const double* sv, int by_col, cudaStream_t s) {
+  long long total = (long long)rows * cols;
+  if (total == 0) return cudaSuccess;
+  scale_rc_kernel<<<grid_for(total), VT, 0, s>>>(a, ld, rows, cols, sv, by_col);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qr(const QrJob* jobs, int njobs, double* ws, cudaStream_t s) {
+  if (njobs == 0) return cudaSuccess;
+  qr_kernel<<<njobs, QRT, 0, s>>>(jobs, ws);
+  return cudaGetLastError();
+}
+
+__global__ void plain_nrm_finalize(const double* partial, int nblk, KrylovState* ks, RhoScalars* rs) {
+  __shared__ double s;
+  finalize_sums(partial, nblk, 1, &s);
+  __syncwarp();
+  if (threadIdx.x != 0) return;
+  double nrm = sqrt(s);
+  ks->nrm = nrm;
+  if (!isfinite(nrm) || nrm == 0.0) {
+    rs->bad = 1;
+    return;
+  }
+  rs->logscale += log(nrm);
+}
+
+cudaError_t k_normalise_inplace(double* v, int64_t n, double* partial, KrylovState* ks, RhoScalars* rs, cudaStream_t s) {
+  int g = grid_for(n);
+  sumsq_kernel<<<g, VT, 0, s>>>(v, n, partial);
+  plain_nrm_finalize<<<1, 32, 0, s>>>(partial, g, ks, rs);
+  scale_kernel<<<g, VT, 0, s>>>(v, n, &ks->nrm, nullptr, v);
+  return cudaGetLastError();
+}
+
+// Normalisation after the Krylov combination: finalize ||y|| then y /= ||y||.
+cudaError_t k_finish_normalise(double* y, int64_t n, double* partial, KrylovState* ks, RhoScalars* rs,
+                               cudaStream_t s) {
+  int g = grid_for(n);
+  nrm_finalize<<<1, 32, 0, s>>>(partial, g, ks, rs);
+  scale_kernel<<<g, VT, 0, s>>>(y, n, &ks->nrm, nullptr, y);
+  return cudaGetLastError();
+}
+
+}  // namespace tt

@@ -1,0 +1,109 @@
+// Launch wrappers of the device kernels (tt_kernels.cu).  Every wrapper is
+// asynchronous on the given stream and returns the cudaError_t of the launch.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tt_core.h"
+
+namespace tt {
+
+// Slot table passed by value to the plan-driven kernels: base pointer of each
+// slot and, for split-BF16 buffers, the element offset of the "lo" half.
+struct Bases {
+  void* p[8];
+  long long lo[8];
+};
+
+// Device copies of a plan.
+struct DevGemm {
+  GGroup* groups = nullptr;
+  GSeg* segs = nullptr;
+  GTile* tiles64 = nullptr;   // 64 x 64 output tiles
+  int ngroups = 0, nsegs = 0, ntiles64 = 0;
+  double flops = 0;
+};
+struct DevGather {
+  GItem* items = nullptr;
+  GContrib* contribs = nullptr;
+  int nitems = 0;
+  double elems = 0;
+};
+struct DevCopy {
+  CItem* items = nullptr;
+  int nitems = 0;
+};
+
+// Device-side Krylov bookkeeping of one Lanczos exponential.
+struct KrylovState {
+  double alpha[17];
+  double beta[17];
+  double h[17];
+  double c[17];
+  double nb;        // ||v||
+  double hscale;    // max(|alpha_j| + beta_j)
+  double resid;     // ||v|| beta_K |c_K|
+  double nrm;       // norm of the result (before normalisation)
+  int kdim;         // Krylov dimension in use
+  int broken;       // breakdown seen
+  int bad;          // NaN / Inf seen
+  int pad;
+};
+
+// Global accumulators of a state (device).
+struct RhoScalars {
+  double logscale;
+  double resid_max;
+  int bad;
+  int pad;
+};
+
+cudaError_t launch_gemm_f64(const DevGemm& g, const Bases& b, cudaStream_t s);
+// nsplit = 2 (3 products) or 3 (6 products); operand level l at offset l * lo[slot]
+cudaError_t launch_gemm_bf16(const DevGemm& g, const Bases& b, int nsplit, cudaStream_t s);
+// in_type / out_type: 0 = double, 1 = float, 2 / 3 = split bf16 with that many levels
+cudaError_t launch_gather(const DevGather& g, const Bases& b, int in_type, int out_type, cudaStream_t s);
+cudaError_t launch_copy(const DevCopy& c, const Bases& b, cudaStream_t s);
+cudaError_t launch_split_bf16(const double* x, int64_t n, int nsplit, void* out /* bf16[nsplit*n] */, cudaStream_t s);
+cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
+
+// Lanczos exponential steps on flat FP64 vectors of length n.  Q holds the
+// Krylov basis with leading dimension ldq.  `partial` is scratch of
+// nblk * 17 doubles.
+int lanczos_nblk();
+cudaError_t k_norm_init(const double* v, int64_t n, double* partial, KrylovState* ks, double* q0, cudaStream_t s);
+cudaError_t k_dots_alpha(const double* Q, int64_t ldq, int k, const double* w, int64_t n, double* partial,
+                         KrylovState* ks, cudaStream_t s);
+cudaError_t k_three_term(const double* Q, int64_t ldq, int k, double* w, int64_t n, KrylovState* ks, cudaStream_t s);
+cudaError_t k_cgs_pass(const double* Q, int64_t ldq, int k, double* w, int64_t n, double* partial, KrylovState* ks,
+                       int last, double breakdown_tol, int K, double* qnext, cudaStream_t s);
+cudaError_t k_krylov_exp(KrylovState* ks, double t, int K, cudaStream_t s);
+cudaError_t k_combine(const double* Q, int64_t ldq, const KrylovState* ks, double* y, int64_t n, double* partial,
+                      KrylovState* ksw, cudaStream_t s);
+// after k_combine (same n): finalize ||y||, logscale += ln ||y||, y /= ||y||
+cudaError_t k_finish_normalise(double* y, int64_t n, double* partial, KrylovState* ks, RhoScalars* rs, cudaStream_t s);
+
+// v /= ||v||, logscale += ln ||v|| (rs->bad set on zero / non-finite norm)
+cudaError_t k_normalise_inplace(double* v, int64_t n, double* partial, KrylovState* ks, RhoScalars* rs, cudaStream_t s);
+
+// Householder QR of a batch of column-major matrices in workspace `ws`.
+cudaError_t launch_qr(const QrJob* jobs, int njobs, double* ws, cudaStream_t s);
+// Sign fix diag(R) >= 0 done inside launch_qr.
+
+// Per-block item of the local measurement (d = 4 local space, <= 4 pairs).
+struct ObsItem {
+  long long off;
+  int dl, m, dr, pad;
+  double wn[4], wd[4];
+};
+// out[0] += sum A T w_n ; out[1] += sum A T w_d  (partial: 2 * nitems doubles)
+cudaError_t launch_local_obs(const ObsItem* items, int nitems, const double* A, const double* T, double* partial,
+                             double* out, cudaStream_t s);
+// column-major a (ld): by_col ? a[:, c] *= s[c] : a[r, :] *= s[r]
+cudaError_t launch_scale_rc(double* a, long long ld, int rows, int cols, const double* sv, int by_col, cudaStream_t s);
+
+// *out = x . y (deterministic two-stage reduction)
+cudaError_t k_dot_plain(const double* x, const double* y, int64_t n, double* partial, double* out, cudaStream_t s);
+
+}  // namespace tt

@@ -1,0 +1,393 @@
+// Host-side plan compilers: every contraction of the sweep written as lists
+// of GEMM groups, W-gather items and strided copies over the U(1)xU(1) blocks.
+//
+// H_eff site apply (Supplement, Fig. "Lanczos": L_i A_i, then H_i, then R_i):
+//   S1  T1[b][(w, a_l), (s_in, b_r)] = L[(w, a_l), b_l] A[b_l, (s_in, b_r)]  per block b
+//   S2  T2[r][(a_l, s_out), (w', b_r)] = sum W[w, sig, tau, w'] T1[...]     (gather)
+//   S3  y[r][(a_l, s_out), a_r] = sum_w' T2[r][:, (w', .)] R[a_r, w', b_r]
+// Left environment update (Fig. "optimalB"(c) contracted with A^L on the bra):
+//   S1, S2, then L'[(w', a_r), b_r] = sum A[(a_l, s), a_r] T2[(a_l, s), (w', b_r)]
+// Right environment update (mirror, A R first):
+//   R1  U1[b][(b_l, s_in), (w', a_r)] = A[(b_l, s_in), b_r] R[(w', a_r), b_r]^T
+//   R2  U2[a][(w, b_l), (s_out, a_r)] = sum W U1                            (gather)
+//   R3  R'[(w, a_l), b_l] = sum A[a_l, (s, a_r)] U2[(w, b_l), (s, a_r)]^T
+// Bond apply (Fig. "optimalB"(d)):
+//   B1  T[(w, a), c] = L[(w, a), b] S[b, c];  B2  y[a, a'] = sum_w T[(w,a), c] R[a', w, c]
+#include "tt_plans.h"
+
+#include <algorithm>
+#include <map>
+#include <stdexcept>
+
+namespace tt {
+
+namespace {
+// (wr, sig) -> terms ; (wl, sig) -> terms
+struct TermIndex {
+  std::map<std::pair<int, int>, std::vector<const MpoTerm*>> by_r, by_l;
+  explicit TermIndex(const std::vector<MpoTerm>& t) {
+    for (const auto& x : t) {
+      by_r[{x.wr, x.sig}].push_back(&x);
+      by_l[{x.wl, x.sig}].push_back(&x);
+    }
+  }
+};
+}  // namespace
+
+SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& ls, const std::vector<MpoTerm>& terms,
+                             const std::vector<Q>& chl, const std::vector<Q>& chr, bool mixed) {
+  SitePlanHost P;
+  P.lay = make_site_layout(BL, BR, ls);
+  const SiteLayout& S = P.lay;
+  EnvLayout EL = make_env_layout(BL, chl);
+  EnvLayout ER = make_env_layout(BR, chr);
+  const int nwl = (int)chl.size(), nwr = (int)chr.size();
+  const int t1flag = mixed ? 2 : 0;
+  TermIndex ti(terms);
+  const int d = ls.d;
+
+  // ---- S1
+  std::vector<int64_t> t1off(S.blk.size(), -1), t1ld(S.blk.size(), 0);
+  int64_t cur = 0;
+  for (size_t bi = 0; bi < S.blk.size(); ++bi) {
+    const SiteBlock& b = S.blk[bi];
+    int64_t M = EL.rows[b.l];
+    int64_t N = (int64_t)b.m * b.dr;
+    if (M == 0 || N == 0) continue;
+    t1off[bi] = cur;
+    t1ld[bi] = N;
+    P.s1.add_group((int)M, (int)N, mkref(S_T1, cur), (int)N, t1flag);
+    P.s1.add_seg(mkref(S_L, EL.off[b.l]), b.dl, 0, mkref(S_X, b.off), (int)N, 0, b.dl);
+    cur += M * N;
+  }
+  P.t1_size = cur;
+
+  // ---- T2 layout (per right sector r of BR)
+  const int nr = BR.nsec();
+  std::vector<int64_t> t2off(nr, 0), t2cols(nr, 0), t2col((size_t)nr * nwr, -1);
+  std::vector<int> t2ket((size_t)nr * nwr, -1);
+  cur = 0;
+  for (int r = 0; r < nr; ++r) {
+    int64_t cols = 0;
+    for (int w = 0; w < nwr; ++w) {
+      int b = BR.find(BR.q[r] - chr[w]);
+      if (b < 0) continue;
+      t2col[(size_t)r * nwr + w] = cols;
+      t2ket[(size_t)r * nwr + w] = b;
+      cols += BR.dim[b];
+    }
+    t2cols[r] = cols;
+    t2off[r] = cur;
+    cur += S.grp_rows[r] * cols;
+  }
+  P.t2_size = cur;
+
+  // ---- S2 gather
+  for (size_t obi = 0; obi < S.blk.size(); ++obi) {
+    const SiteBlock& ob = S.blk[obi];
+    const int r = ob.r;
+    for (int so = 0; so < ob.m; ++so) {
+      const int sig = ls.pairs[ob.p][so].first, sgp = ls.pairs[ob.p][so].second;
+      for (int w2 = 0; w2 < nwr; ++w2) {
+        int64_t col = t2col[(size_t)r * nwr + w2];
+        if (col < 0) continue;
+        const int br = t2ket[(size_t)r * nwr + w2];
+        GItem it;
+        it.dst = mkref(S_T2, t2off[r] + (ob.grp_row + so) * t2cols[r] + col);
+        it.dst_rs = (int64_t)ob.m * t2cols[r];
+        it.rows = ob.dl;
+        it.cols = BR.dim[br];
+        it.c0 = (int)P.s2.contribs.size();
+        auto f = ti.by_r.find({w2, sig});
+        if (f != ti.by_r.end())
+          for (const MpoTerm* t : f->second) {
+            const int w = t->wl, tau = t->tau;
+            int lb = BL.find(BL.q[ob.l] - chl[w]);
+            if (lb < 0) continue;
+            const int pidx = tau * d + sgp;
+            const int pin = ls.sec_of[pidx], si = ls.pos_of[pidx];
+            int bin = S.block_of(lb, pin);
+            if (bin < 0 || t1off[bin] < 0) continue;
+            if (S.blk[bin].r != br) throw std::logic_error("S2: charge mismatch");
+            int64_t row = EL.row_of(lb, w);
+            if (row < 0) continue;
+            GContrib c;
+            c.src = mkref(S_T1, t1off[bin] + row * t1ld[bin] + (int64_t)si * S.blk[bin].dr);
+            c.src_rs = t1ld[bin];
+            c.coef = t->v;
+            P.s2.contribs.push_back(c);
+          }
+        it.c1 = (int)P.s2.contribs.size();
+        P.s2.items.push_back(it);
+        P.s2.elems += (double)it.rows * it.cols * (1 + it.c1 - it.c0);
+      }
+    }
+  }
+
+  // ---- S3 (H_eff output) and S3L (left environment update)
+  for (int r = 0; r < nr; ++r) {
+    if (S.grp_rows[r] > 0) {
+      P.s3.add_group((int)S.grp_rows[r], BR.dim[r], mkref(S_Y, S.grp_off[r]), BR.dim[r], 0);
+      for (int w2 = 0; w2 < nwr; ++w2) {
+        int64_t col = t2col[(size_t)r * nwr + w2];
+        if (col < 0) continue;
+        const int b = t2ket[(size_t)r * nwr + w2];
+        int64_t rrow = ER.row_of(b, w2);
+        P.s3.add_seg(mkref(S_T2, t2off[r] + col), (int)t2cols[r], 0, mkref(S_R, ER.off[b] + rrow * BR.dim[b]),
+                     BR.dim[b], 1, BR.dim[b]);
+      }
+    }
+    for (int w2 = 0; w2 < nwr; ++w2) {
+      int64_t col = t2col[(size_t)r * nwr + w2];
+      if (col < 0) continue;
+      const int b = t2ket[(size_t)r * nwr + w2];
+      int64_t lrow = ER.row_of(b, w2);
+      P.s3l.add_group(BR.dim[r], BR.dim[b], mkref(S_Y, ER.off[b] + lrow * BR.dim[b]), BR.dim[b], 0);
+      if (S.grp_rows[r] > 0)
+        P.s3l.add_seg(mkref(S_X, S.grp_off[r]), BR.dim[r], 1, mkref(S_T2, t2off[r] + col), (int)t2cols[r], 0,
+                      (int)S.grp_rows[r]);
+    }
+  }
+  P.lenv_size = ER.size;
+
+  // ---- R1
+  std::vector<int64_t> u1off(S.blk.size(), -1), u1ld(S.blk.size(), 0);
+  cur = 0;
+  for (size_t bi = 0; bi < S.blk.size(); ++bi) {
+    const SiteBlock& b = S.blk[bi];
+    int64_t M = (int64_t)b.dl * b.m;
+    int64_t N = ER.rows[b.r];
+    if (M == 0 || N == 0) continue;
+    u1off[bi] = cur;
+    u1ld[bi] = N;
+    P.r1.add_group((int)M, (int)N, mkref(S_T1, cur), (int)N, t1flag);
+    P.r1.add_seg(mkref(S_X, b.off), b.dr, 0, mkref(S_R, ER.off[b.r]), b.dr, 1, b.dr);
+    cur += M * N;
+  }
+  P.u1_size = cur;
+
+  // ---- U2 layout per bra-left sector a of BL: rows (w, b_l), cols (p, s, a_r)
+  const int nl = BL.nsec();
+  std::vector<int64_t> u2off(nl, 0), u2rows(nl, 0), u2cols(nl, 0);
+  std::vector<int64_t> u2row((size_t)nl * nwl, -1);
+  std::vector<int> u2ket((size_t)nl * nwl, -1);
+  std::vector<int64_t> colseg((size_t)nl * S.npq, -1);
+  cur = 0;
+  for (int a = 0; a < nl; ++a) {
+    int64_t rows = 0, cols = 0;
+    for (int w = 0; w < nwl; ++w) {
+      int lb = BL.find(BL.q[a] - chl[w]);
+      if (lb < 0) continue;
+      u2row[(size_t)a * nwl + w] = rows;
+      u2ket[(size_t)a * nwl + w] = lb;
+      rows += BL.dim[lb];
+    }
+    for (int p = 0; p < S.npq; ++p) {
+      int bi = S.block_of(a, p);
+      if (bi < 0) continue;
+      colseg[(size_t)a * S.npq + p] = cols;
+      cols += (int64_t)S.blk[bi].m * S.blk[bi].dr;
+    }
+    u2off[a] = cur;
+    u2rows[a] = rows;
+    u2cols[a] = cols;
+    cur += rows * cols;
+  }
+  P.u2_size = cur;
+
+  // ---- R2 gather
+  for (int a = 0; a < nl; ++a)
+    for (int w = 0; w < nwl; ++w) {
+      int64_t row0 = u2row[(size_t)a * nwl + w];
+      if (row0 < 0) continue;
+      const int lb = u2ket[(size_t)a * nwl + w];
+      for (int p = 0; p < S.npq; ++p) {
+        int obi = S.block_of(a, p);
+        if (obi < 0) continue;
+        const SiteBlock& ob = S.blk[obi];
+        for (int so = 0; so < ob.m; ++so) {
+          const int sig = ls.pairs[p][so].first, sgp = ls.pairs[p][so].second;
+          GItem it;
+          it.dst = mkref(S_T2, u2off[a] + row0 * u2cols[a] + colseg[(size_t)a * S.npq + p] + (int64_t)so * ob.dr);
+          it.dst_rs = u2cols[a];
+          it.rows = BL.dim[lb];
+          it.cols = ob.dr;
+          it.c0 = (int)P.r2.contribs.size();
+          auto f = ti.by_l.find({w, sig});
+          if (f != ti.by_l.end())
+            for (const MpoTerm* t : f->second) {
+              const int w2 = t->wr, tau = t->tau;
+              const int pidx = tau * d + sgp;
+              const int pin = ls.sec_of[pidx], si = ls.pos_of[pidx];
+              int bin = S.block_of(lb, pin);
+              if (bin < 0 || u1off[bin] < 0) continue;
+              const SiteBlock& ib = S.blk[bin];
+              int64_t rrow = ER.row_of(ib.r, w2);
+              if (rrow < 0) continue;
+              if (ER.bra[(size_t)ib.r * ER.nw + w2] != ob.r) throw std::logic_error("R2: charge mismatch");
+              GContrib c;
+              c.src = mkref(S_T1, u1off[bin] + (int64_t)si * u1ld[bin] + rrow);
+              c.src_rs = (int64_t)ib.m * u1ld[bin];
+              c.coef = t->v;
+              P.r2.contribs.push_back(c);
+            }
+          it.c1 = (int)P.r2.contribs.size();
+          P.r2.items.push_back(it);
+          P.r2.elems += (double)it.rows * it.cols * (1 + it.c1 - it.c0);
+        }
+      }
+    }
+
+  // ---- R3 (right environment of bond j, layout EL)
+  for (int a = 0; a < nl; ++a)
+    for (int w = 0; w < nwl; ++w) {
+      int64_t row0 = u2row[(size_t)a * nwl + w];
+      if (row0 < 0) continue;
+      const int lb = u2ket[(size_t)a * nwl + w];
+      int64_t erow = EL.row_of(lb, w);
+      P.r3.add_group(BL.dim[a], BL.dim[lb], mkref(S_Y, EL.off[lb] + erow * BL.dim[lb]), BL.dim[lb], 0);
+      for (int p = 0; p < S.npq; ++p) {
+        int obi = S.block_of(a, p);
+        if (obi < 0) continue;
+        const SiteBlock& ob = S.blk[obi];
+        int K = ob.m * ob.dr;
+        P.r3.add_seg(mkref(S_X, ob.off), K, 0,
+                     mkref(S_T2, u2off[a] + row0 * u2cols[a] + colseg[(size_t)a * S.npq + p]), (int)u2cols[a], 1, K);
+      }
+    }
+  P.renv_size = EL.size;
+  return P;
+}
+
+BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch) {
+  BondPlanHost P;
+  EnvLayout E = make_env_layout(B, ch);
+  P.mat = make_bondmat_layout(B);
+  const int nw = (int)ch.size();
+  std::vector<int64_t> toff(B.nsec(), -1);
+  int64_t cur = 0;
+  for (int b = 0; b < B.nsec(); ++b) {
+    if (E.rows[b] == 0) continue;
+    toff[b] = cur;
+    P.b1.add_group((int)E.rows[b], B.dim[b], mkref(S_T1, cur), B.dim[b], 0);
+    P.b1.add_seg(mkref(S_L, E.off[b]), B.dim[b], 0, mkref(S_X, P.mat.off[b]), B.dim[b], 0, B.dim[b]);
+    cur += E.rows[b] * B.dim[b];
+  }
+  P.t_size = cur;
+  for (int q = 0; q < B.nsec(); ++q) {
+    P.b2.add_group(B.dim[q], B.dim[q], mkref(S_Y, P.mat.off[q]), B.dim[q], 0);
+    for (int w = 0; w < nw; ++w) {
+      int b = B.find(B.q[q] - ch[w]);
+      if (b < 0 || toff[b] < 0) continue;
+      int64_t row = E.row_of(b, w);
+      P.b2.add_seg(mkref(S_T2, toff[b] + row * B.dim[b]), B.dim[b], 0, mkref(S_R, E.off[b] + row * B.dim[b]),
+                   B.dim[b], 1, B.dim[b]);
+    }
+  }
+  return P;
+}
+
+GemmPlan build_absorb_left(const SiteLayout& oldl, const SiteLayout& newl, const Bond& Bold, const Bond& Bnew,
+                           const std::vector<int64_t>& soff, const std::vector<int>& new_of_old) {
+  // A_new[(l', p, r)] = S_l (d_new x d_old, row-major) A_old[(l, p, r)] ; l' = new_of_old[l]
+  GemmPlan G;
+  for (const SiteBlock& ob : oldl.blk) {
+    int ln = new_of_old[ob.l];
+    if (ln < 0) continue;
+    int nbi = newl.block_of(ln, ob.p);
+    if (nbi < 0) continue;
+    const SiteBlock& nb = newl.blk[nbi];
+    int N = ob.m * ob.dr;
+    G.add_group(Bnew.dim[ln], N, mkref(S_Y, nb.off), N, 0);
+    G.add_seg(mkref(S_AUX, soff[ob.l]), Bold.dim[ob.l], 0, mkref(S_X, ob.off), N, 0, Bold.dim[ob.l]);
+  }
+  return G;
+}
+
+GemmPlan build_absorb_right(const SiteLayout& oldl, const SiteLayout& newl, const Bond& Bold, const Bond& Bnew,
+                            const std::vector<int64_t>& soff, const std::vector<int>& new_of_old) {
+  // A_new[group r'] = A_old[group r] (rows x d_old) S_r (d_old x d_new, row-major)
+  GemmPlan G;
+  for (int r = 0; r < Bold.nsec(); ++r) {
+    int rn = new_of_old[r];
+    if (rn < 0) continue;
+    if (oldl.grp_rows[r] == 0) continue;
+    G.add_group((int)oldl.grp_rows[r], Bnew.dim[rn], mkref(S_Y, newl.grp_off[rn]), Bnew.dim[rn], 0);
+    G.add_seg(mkref(S_X, oldl.grp_off[r]), Bold.dim[r], 0, mkref(S_AUX, soff[r]), Bnew.dim[rn], 0, Bold.dim[r]);
+  }
+  return G;
+}
+
+QrPlanHost build_qr_left(const SiteLayout& S, const Bond& BR) {
+  // per right sector r: the (grp_rows x d_r) group matrix, QR -> A^L, R -> S
+  QrPlanHost P;
+  int64_t ws = 0, sm = 0;
+  for (int r = 0; r < BR.nsec(); ++r) {
+    int m = (int)S.grp_rows[r], n = BR.dim[r];
+    QrJob J;
+    J.m = m;
+    J.n = n;
+    J.a = ws;
+    ws += (int64_t)m * n;
+    J.q = ws;
+    ws += (int64_t)m * n;
+    J.r = ws;
+    ws += (int64_t)n * n;
+    P.jobs.push_back(J);
+    P.gather.items.push_back(CItem{mkref(S_X, S.grp_off[r]), mkref(S_AUX2, J.a), n, 1, 1, m, m, n});
+    P.scatter.items.push_back(CItem{mkref(S_AUX2, J.q), mkref(S_Y, S.grp_off[r]), 1, m, n, 1, m, n});
+    P.rout.items.push_back(CItem{mkref(S_AUX2, J.r), mkref(S_AUX, sm), 1, n, n, 1, n, n});
+    P.new_dim.push_back(n);
+    sm += (int64_t)n * n;
+  }
+  P.ws_size = ws;
+  P.s_size = sm;
+  return P;
+}
+
+QrPlanHost build_lq_right(const SiteLayout& S, const Bond& BL, bool shrink) {
+  // per left sector l: M = [blocks (l, p)] (d_l x cols); QR of M^T (cols x d_l).
+  QrPlanHost P;
+  int64_t ws = 0, sm = 0;
+  for (int l = 0; l < BL.nsec(); ++l) {
+    int n = BL.dim[l];
+    int64_t cols = 0;
+    std::vector<std::pair<int, int64_t>> segs;
+    for (int p = 0; p < S.npq; ++p) {
+      int bi = S.block_of(l, p);
+      if (bi < 0) continue;
+      segs.push_back({bi, cols});
+      cols += (int64_t)S.blk[bi].m * S.blk[bi].dr;
+    }
+    int m = (int)cols;
+    int k = shrink ? std::min(m, n) : n;
+    QrJob J;
+    J.m = m;
+    J.n = n;
+    J.a = ws;
+    ws += (int64_t)m * n;
+    J.q = ws;
+    ws += (int64_t)m * n;
+    J.r = ws;
+    ws += (int64_t)n * n;
+    P.jobs.push_back(J);
+    for (auto& sg : segs) {
+      const SiteBlock& b = S.blk[sg.first];
+      int C = b.m * b.dr;
+      // block row-major (d_l x C) -> M^T column-major rows [cs, cs + C), cols a_l
+      P.gather.items.push_back(CItem{mkref(S_X, b.off), mkref(S_AUX2, J.a + sg.second), C, 1, m, 1, n, C});
+      // A^R block (first k rows a_l) = Q'^T
+      P.scatter_blocks.push_back({sg.first, sg.second});
+    }
+    P.lq_cols.push_back(m);
+    P.new_dim.push_back(k);
+    // S = R'^T (n x k, row-major): S[a][b] = R'[b][a] = ws[r + b + a n]
+    P.rout.items.push_back(CItem{mkref(S_AUX2, J.r), mkref(S_AUX, sm), n, 1, k, 1, n, k});
+    sm += (int64_t)n * k;
+  }
+  P.ws_size = ws;
+  P.s_size = sm;
+  return P;
+}
+
+}  // namespace tt

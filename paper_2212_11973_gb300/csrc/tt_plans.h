@@ -1,0 +1,40 @@
+// Plan compilers (host).  See tt_plans.cpp for the contraction stages.
+#pragma once
+#include "tt_core.h"
+
+namespace tt {
+
+struct SitePlanHost {
+  SiteLayout lay;
+  GemmPlan s1, s3, s3l, r1, r3;
+  GatherPlan s2, r2;
+  int64_t t1_size = 0, t2_size = 0, u1_size = 0, u2_size = 0;
+  int64_t lenv_size = 0, renv_size = 0;
+};
+
+struct BondPlanHost {
+  BondMatLayout mat;
+  GemmPlan b1, b2;
+  int64_t t_size = 0;
+};
+
+struct QrPlanHost {
+  std::vector<QrJob> jobs;
+  CopyPlan gather, scatter, rout;
+  std::vector<std::pair<int, int64_t>> scatter_blocks;  // LQ: (old block, column offset in M)
+  std::vector<int> lq_cols;                             // LQ: columns of M per left sector
+  std::vector<int> new_dim;                             // bond dims after the move
+  int64_t ws_size = 0, s_size = 0;
+};
+
+SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& ls, const std::vector<MpoTerm>& terms,
+                             const std::vector<Q>& chl, const std::vector<Q>& chr, bool mixed);
+BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch);
+GemmPlan build_absorb_left(const SiteLayout& oldl, const SiteLayout& newl, const Bond& Bold, const Bond& Bnew,
+                           const std::vector<int64_t>& soff, const std::vector<int>& new_of_old);
+GemmPlan build_absorb_right(const SiteLayout& oldl, const SiteLayout& newl, const Bond& Bold, const Bond& Bnew,
+                            const std::vector<int64_t>& soff, const std::vector<int>& new_of_old);
+QrPlanHost build_qr_left(const SiteLayout& S, const Bond& BR);
+QrPlanHost build_lq_right(const SiteLayout& S, const Bond& BL, bool shrink);
+
+}  // namespace tt

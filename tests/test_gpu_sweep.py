@@ -1,0 +1,112 @@
+"""GPU parity: the CUDA tanTRG path against the CPU oracle on the same inputs.
+
+FP64 path: relative difference <= 1e-10 in energy and free energy per site
+(and density, double occupancy).  Mixed path (split-BF16 x6): <= 1e-6 in
+energy and double occupancy.  Both sides run the same algorithm (growth with
+2-TDVP, then 1-TDVP, K = 8, tau = dtau / 4 per half sweep).
+"""
+import pytest
+
+from paper_2212_11973_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+KEYS_FP64 = ("energy_per_site", "free_energy_per_site", "density", "double_occ", "lnZ")
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def tt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_11973_gb300 import tantrg
+    tantrg.load_library()
+    return tantrg
+
+
+@pytest.fixture(scope="module")
+def ctx(tt):
+    c = tt.Context()
+    yield c
+    c.close()
+
+
+def _gpu_run(tt, ctx, cfg, beta_end, precision=None, D=None):
+    mpo = tt.Mpo(ctx, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
+    D = D or cfg.D
+    prec = cfg.precision if precision is None else precision
+    rho = tt.Rho(ctx, mpo, cfg.beta0, tt.run_opts(D, cfg.krylov, prec))
+    rho.grow(cfg.dtau, 1.0)
+    obs = [rho.measure()]
+    while obs[-1]["beta"] < beta_end - 1e-9:
+        rho.step(cfg.dtau, 1)
+        obs.append(rho.measure())
+    dims = rho.bond_dims()
+    rho.close()
+    mpo.close()
+    return obs, dims
+
+
+def _oracle_run(cfg, beta_end, D=None):
+    from oracle import model as om
+    from oracle import mpo as ompo
+    from oracle import tantrg as ot
+    m = om.Model(cfg.Lx, cfg.Wy, cfg.periodic, cfg.t, cfg.U, cfg.mu, cfg.form)
+    rec = {}
+
+    def cb(st, stage):
+        rec[round(st.beta, 9)] = ot.measure(st)
+
+    st = ot.run(ompo.hubbard_mpo(m), cfg.beta0, cfg.dtau, beta_end, ot.TruncOpts(D or cfg.D), K=cfg.krylov, callback=cb)
+    return rec, st
+
+
+def test_cluster_2x2_fp64_matches_oracle(tt, ctx):
+    cfg = wl.CLUSTER_2x2
+    gpu, dims = _gpu_run(tt, ctx, cfg, 1.01)
+    ref, st = _oracle_run(cfg, 1.01)
+    assert dims[1:-1] == st.bond_dims()
+    for o in gpu:
+        r = ref[round(o["beta"], 9)]
+        for k in KEYS_FP64:
+            assert _rel(o[k], r[k]) < 1e-10, (o["beta"], k, o[k], r[k])
+
+
+def test_cluster_2x2_untruncated_matches_oracle(tt, ctx):
+    """Full rank (D = 256, bonds 16/256/16): GPU FP64 against the oracle."""
+    cfg = wl.CLUSTER_2x2_FULL
+    gpu, dims = _gpu_run(tt, ctx, cfg, 0.51)
+    ref, st = _oracle_run(cfg, 0.51)
+    assert dims == [1, 16, 256, 16, 1] and st.bond_dims() == [16, 256, 16]
+    for o in gpu:
+        r = ref[round(o["beta"], 9)]
+        for k in KEYS_FP64:
+            assert _rel(o[k], r[k]) < 1e-10, (o["beta"], k, o[k], r[k])
+
+
+def test_ladder_fp64_matches_oracle(tt, ctx):
+    """2x4 ladder at D = 32: several sectors per bond, truncated growth."""
+    cfg = wl.LADDER_2x4
+    gpu, dims = _gpu_run(tt, ctx, cfg, 0.51)
+    ref, st = _oracle_run(cfg, 0.51)
+    assert dims[1:-1] == st.bond_dims()
+    for o in gpu:
+        r = ref[round(o["beta"], 9)]
+        for k in KEYS_FP64:
+            assert _rel(o[k], r[k]) < 1e-10, (o["beta"], k, o[k], r[k])
+
+
+@pytest.mark.parametrize("prec,tol", [(2, 1e-6)])
+def test_ladder_mixed_matches_oracle(tt, ctx, prec, tol):
+    cfg = wl.LADDER_2x4
+    gpu, dims = _gpu_run(tt, ctx, cfg, 0.51, precision=prec)
+    ref, st = _oracle_run(cfg, 0.51)
+    assert dims[1:-1] == st.bond_dims()
+    for o in gpu:
+        r = ref[round(o["beta"], 9)]
+        for k in ("energy_per_site", "double_occ"):
+            assert _rel(o[k], r[k]) < tol, (o["beta"], k, o[k], r[k])

@@ -2,10 +2,10 @@
 
 The strongest pin is tangent-space exactness (Supplement, "Splitting method"):
 with bond dimensions at their maximum the 1-TDVP/2-TDVP integrators carry no
-projection error, so the oracle must reproduce exact diagonalisation of the
-same initial state, exp(-(beta-beta0) H/2)(I - beta0 H/2), to rounding and
-Krylov error.  Planted mistakes (wrong step length, wrong bond-step sign)
-must break it.
+projection error, so the oracle started from the initial state padded to
+maximal bonds must reproduce exact diagonalisation of the same initial
+state, exp(-(beta-beta0) H/2)(I - beta0 H/2), to rounding and Krylov error.
+Planted mistakes (wrong step length, wrong bond-step sign) must break it.
 """
 import math
 
@@ -26,7 +26,7 @@ def _rel(a, b):
 
 def _run_vs_ed(m, D, beta_end, tol, beta0=0.01, dtau=0.05):
     W = ompo.hubbard_mpo(m)
-    st = tt.run(W, beta0, dtau, beta_end, tt.TruncOpts(D))
+    st = tt.run(W, beta0, dtau, beta_end, tt.TruncOpts(D), pad_full=True)
     ob = tt.measure(st)
     ed = om.ed_thermo(m, [st.beta], beta0=beta0)[0]
     for k in KEYS:
@@ -63,7 +63,7 @@ def test_planted_wrong_step_length_is_caught(monkeypatch):
     monkeypatch.setattr(tt, "tdvp1_step", broken)
     m = om.Model(1, 3, False, U=3.0, mu=0.4, form=0)
     W = ompo.hubbard_mpo(m)
-    st = tt.run(W, 0.01, 0.05, 0.51, tt.TruncOpts(16))
+    st = tt.run(W, 0.01, 0.05, 0.51, tt.TruncOpts(16), pad_full=True)
     ob = tt.measure(st)
     ed = om.ed_thermo(m, [st.beta], beta0=0.01)[0]
     assert _rel(ob["lnZ"], ed["lnZ"]) > 1e-3
@@ -80,10 +80,36 @@ def test_planted_wrong_bond_sign_is_caught(monkeypatch):
     monkeypatch.setattr(tt, "_bond_exp", broken)
     m = om.Model(1, 3, False, U=3.0, mu=0.4, form=0)
     W = ompo.hubbard_mpo(m)
-    st = tt.run(W, 0.01, 0.05, 0.51, tt.TruncOpts(16))
+    st = tt.run(W, 0.01, 0.05, 0.51, tt.TruncOpts(16), pad_full=True)
     ob = tt.measure(st)
     ed = om.ed_thermo(m, [st.beta], beta0=0.01)[0]
     assert _rel(ob["energy_per_site"], ed["energy_per_site"]) > 1e-4
+
+
+def test_full_rank_two_site_growth_is_exact():
+    """2-TDVP steps on the padded state (nothing truncated) are exact as well."""
+    m = om.Model(1, 3, False, U=3.0, mu=0.4, form=0)
+    st = tt.pad_to_full_rank(tt.init_state(ompo.hubbard_mpo(m), 0.01))
+    for _ in range(3):
+        tt.tdvp2_step(st, 0.05, tt.TruncOpts(16, svd_cut=0.0))
+    for _ in range(3):
+        tt.tdvp1_step(st, 0.05)
+    ob = tt.measure(st)
+    ed = om.ed_thermo(m, [st.beta], beta0=0.01)[0]
+    for k in KEYS:
+        assert _rel(ob[k], ed[k]) < 1e-10, (k, ob[k], ed[k])
+
+
+def test_compact_initial_state():
+    """The compact rho_0 has the operator Schmidt ranks of I - beta0 H/2:
+    2 + 4 x (distinct left ends of hopping bonds crossing the cut), minus
+    dependencies (the last cut of the 2x2 cluster sees one right site)."""
+    m = om.Model(2, 2, False, U=4.0, mu=0.0, form=1)
+    st = tt.init_state(ompo.hubbard_mpo(m), 0.01)
+    assert st.bond_dims() == [6, 10, 6]
+    padded = tt.pad_to_full_rank(tt.init_state(ompo.hubbard_mpo(m), 0.01))
+    assert padded.bond_dims() == [16, 256, 16]
+    assert abs(tt.measure(padded)["lnZ"] - tt.measure(st)["lnZ"]) < 1e-12
 
 
 def test_initial_state_is_first_order_expansion():
@@ -172,6 +198,8 @@ def test_truncation_rule():
     assert tt.truncation_rank(s2, 2, 1e-14, 1e-10) == 3       # leading group kept whole
     s3 = np.array([1.0, 1e-9, 1e-9 * (1 + 1e-7), 1e-12])
     assert tt.truncation_rank(s3, 2, 0.0, 1e-10) == 1         # absolute guard groups them
+    s4 = np.array([1.0, 1e-6, 1e-6 * (1 - 1e-7), 1e-12])
+    assert tt.truncation_rank(s4, 2, 0.0, 1e-10) == 2         # 1e-13 apart: not grouped
 
 
 def test_free_fermion_ladder_error_decreases_with_D():
