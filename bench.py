@@ -1,0 +1,289 @@
+"""Benchmark: seconds per 1-TDVP beta-step and site-H_eff TFLOP/s at D = 1024.
+
+Workload (default): CL6x12 Hubbard cylinder (width 6 periodic, length 12,
+snake order, N = 72), t = 1, U = 8, mu for about 1/8 hole doping (particle-hole
+symmetric form), block-sparse U(1)xU(1) MPO rho_h with D = 1024, dtau = 0.05,
+Krylov K = 8, split-BF16 x6 tensor-core contractions with FP64 Lanczos, QR,
+exponential and log-norm.
+
+Preparation (untimed): rho_h(beta0) = I - beta0 H/2, 2-TDVP growth at
+D_grow = 256, zero-weight padding of every bond to D = 1024, W warm-up
+beta-steps (which populate the padded directions).  Timed: K beta-steps
+(each an L->R plus an R->L 1-TDVP half sweep with tau = dtau/4), CUDA events
+on the library stream, barrier + synchronize on both sides, max over ranks.
+The state (> 1 GB) is far larger than L2, so no flush is needed.
+
+Multi-GPU: replicas only (the sweep is sequential along the chain); each rank
+evolves its own copy and `value` is the whole-job seconds per beta-step.
+
+--impl reference times the CPU oracle (dense FP64 NumPy) on a bounded sample
+of the same workload: one dense site H_eff apply at D = 512 with the oracle's
+MPO, scaled by (1024/512)^3 and by the 2N(K+1) site-apply equivalents of a
+beta-step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TDVP s per beta-step & H_eff TFLOP/s at D=1024; mixed vs FP64 at 1e-6 rel err"
+UNIT = "s/beta-step"
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(D: int = 512, seed: int = 7):
+    """One dense FP64 site H_eff apply of the oracle at bond dimension D with the
+    CL6x12 MPO (random dense environments and site tensor); returns seconds."""
+    import numpy as np
+    from oracle import model as om
+    from oracle import mpo as ompo
+    from oracle import tantrg as ot
+    from paper_2212_11973_gb300 import workloads as wl
+    cfg = wl.CYL_6x12_D1024
+    m = om.Model(cfg.Lx, cfg.Wy, cfg.periodic, cfg.t, cfg.U, cfg.mu, cfg.form)
+    W = ompo.hubbard_mpo(m)[cfg.N // 2]
+    DH = W.shape[0]
+    rng = np.random.default_rng(seed)
+    L = rng.standard_normal((D, DH, D))
+    R = rng.standard_normal((D, DH, D))
+    x = rng.standard_normal((D, 4, 4, D))
+    t0 = time.perf_counter()
+    ot.heff_site(L, W, R, x)
+    return time.perf_counter() - t0, DH
+
+
+def reference_arm(args):
+    """The oracle timed on the host cores, per 'step' one bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2212_11973_gb300 import workloads as wl
+    cfg = wl.CYL_6x12_D1024
+    Ds = 512
+    scale = (cfg.D / Ds) ** 3 * 2 * cfg.N * (cfg.krylov + 1)
+    for _ in range(args.warmup):
+        oracle_sample(Ds)
+    ts = [oracle_sample(Ds)[0] for _ in range(args.steps)]
+    per_step = statistics.mean(ts) * scale
+    cores = os.cpu_count()
+    sample = (f"one dense FP64 site H_eff apply at D={Ds} (oracle MPO of CL6x12), scaled by "
+              f"(1024/{Ds})^3 x 2N(K+1)={2 * cfg.N * (cfg.krylov + 1)} applies per beta-step")
+    line = {"impl": "reference", "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "N": cfg.N, "D": cfg.D, "dtau": cfg.dtau, "krylov": cfg.krylov},
+            "cpu_baseline": {"value": per_step, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": per_step, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--D", type=int, default=None, help="override the bond dimension (debug)")
+    ap.add_argument("--grow-D", type=int, default=256)
+    ap.add_argument("--workload", default="cl6x12", choices=["cl6x12", "cl4x8", "cl4x8-mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2212_11973_gb300 import tantrg as tt
+    from paper_2212_11973_gb300 import workloads as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    cfg = {"cl6x12": wl.CYL_6x12_D1024, "cl4x8": wl.CYL_4x8_D256, "cl4x8-mixed": wl.CYL_4x8_D512}[args.workload]
+    D = args.D or cfg.D
+    prec = cfg.precision
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = tt.Context(stream=stream)
+        mpo = tt.Mpo(ctx, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
+        t_prep = time.perf_counter()
+        gD = min(args.grow_D, D)
+        rho = tt.Rho(ctx, mpo, cfg.beta0, tt.run_opts(gD, cfg.krylov, prec, growth_precision=prec))
+        rho.grow(cfg.dtau, 1.0)
+        if gD < D:
+            rho.pad(D)
+        for _ in range(args.warmup):
+            rho.step(cfg.dtau, 1)
+        torch.cuda.synchronize()
+        t_prep = time.perf_counter() - t_prep
+        dims = rho.bond_dims()
+
+        # ---- timed region (device) ----
+        rho.set_profiling(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        rho.stats()  # reset the accumulators
+        torch.cuda.profiler.start()  # ncu --profile-from-start off captures only this region
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                rho.step(cfg.dtau, 1)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        s = rho.stats()  # per-launch event times accumulated over the K steps
+        flops, heff_ms, heff_n = s["heff_flops"], s["heff_ms"], s["heff_launches"]
+        env_ms, env_fl, launches = s["env_ms"], s["env_flops"], s["launches"]
+        barrier()
+        t_dev = ev0.elapsed_time(ev1) / 1e3
+        rho.set_profiling(False)
+        t_max = t_dev
+        if world > 1:
+            tmax = torch.tensor([t_dev], device="cuda")
+            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+            t_max = float(tmax.item())
+        per_step = t_max / (args.steps * world)
+
+        # ---- end to end through the public API (host wall clock) ----
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        obs = None
+        for _ in range(args.steps):
+            rho.step(cfg.dtau, 1)
+            obs = rho.measure()  # synchronises; device -> host copy of the observables
+        e2e = (time.perf_counter() - t0) / (args.steps * world)
+        barrier()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    heff_tflops = flops / (heff_ms / 1e3) / 1e12 if heff_ms > 0 else None
+    if peaks:
+        peak = peaks["bf16_tflops_sustained"]
+        peak_note = "of measured (bf16 sustained, MEASURED_PEAKS.json)"
+    else:
+        peak, peak_note = 1700.0, "of fallback"
+    roofline = {"bound": "tensor", "kernel": "site H_eff split-BF16 GEMMs (S1 + S3)",
+                "achieved": heff_tflops, "peak": peak, "unit": "TFLOP/s",
+                "frac": (heff_tflops / peak) if heff_tflops else None,
+                "flops_per_launch": flops / max(heff_n, 1), "avg_launch_ms": heff_ms / max(heff_n, 1),
+                "executed_over_algorithmic": 6 if prec == 2 else (3 if prec == 1 else 1),
+                "peak_note": peak_note, "traffic": None}
+    cpu = None
+    if not args.no_cpu_baseline:
+        Ds = 512
+        ts = [oracle_sample(Ds)[0] for _ in range(2)]
+        scale = (cfg.D / Ds) ** 3 * 2 * cfg.N * (cfg.krylov + 1)
+        cpu = {"value": min(ts) * scale, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one dense FP64 site H_eff apply at D={Ds} (oracle MPO of CL6x12), scaled by "
+                         f"(1024/{Ds})^3 x 2N(K+1) site-apply equivalents per beta-step"}
+    line = {
+        "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {0: "f64", 1: "bf16x3+f64", 2: "bf16x6+f64"}[prec], "data": "synthetic",
+        "config": {"workload": cfg.name, "N": cfg.N, "D": D, "max_bond": max(dims), "dtau": cfg.dtau,
+                   "krylov": cfg.krylov, "U": cfg.U, "mu": cfg.mu, "parallelism": f"replicas x{world}",
+                   "prep": f"2-TDVP growth at D={gD}, padded to D={D}, {args.warmup} warm-up steps ({t_prep:.1f} s)",
+                   "l2": "state larger than L2 (no flush)"},
+        "heff_tflops": heff_tflops, "env_tflops": (env_fl / (env_ms / 1e3) / 1e12) if env_ms > 0 else None,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 56,
+                "includes": "tt_tdvp_step + tt_measure (measurement sweep and observables to host)"},
+        "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
+        "observables": {k: obs[k] for k in ("beta", "energy_per_site", "density", "double_occ",
+                                            "free_energy_per_site")} if obs else None,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

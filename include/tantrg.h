@@ -112,13 +112,18 @@ typedef struct {
 } tt_obs;
 
 typedef struct {
-  double heff_flops;       /* algorithmic flops of the site H_eff applies of the last tt_tdvp_step */
-  double heff_ms;          /* summed device time of those applies (CUDA events) */
-  double step_flops;       /* algorithmic flops of all contractions of the last step */
-  double step_ms;          /* device time of the last step */
-  double bytes_lanczos;    /* algorithmic bytes moved by Lanczos vector kernels, last step */
-  double lanczos_ms;       /* their device time */
-  long long launches;      /* kernels launched by the last step */
+  double heff_flops;       /* algorithmic flops (2 M N K over the blocks) of the
+                              site H_eff GEMM launches of the last tt_tdvp_step */
+  double heff_ms;          /* summed device time of those launches (CUDA events,
+                              profiling mode only, else 0) */
+  long long heff_launches; /* number of those launches (profiling mode) */
+  double env_flops, env_ms;/* same for the environment-update GEMMs */
+  double bond_ms;          /* bond H_eff GEMMs (profiling mode) */
+  double gather_ms;        /* W-gather kernels (profiling mode) */
+  long long gather_launches;
+  double step_flops;       /* algorithmic flops of all contractions of the last call */
+  double step_ms;          /* device time of the last tt_tdvp_step call (events) */
+  long long launches;      /* kernels launched by the last tt_tdvp_step call */
   int n_sites, max_bond, n_sectors_max;
 } tt_stats;
 
@@ -154,6 +159,13 @@ void tt_rho_destroy(tt_rho* rho);
 tt_status tt_rho_grow(tt_rho* rho, const tt_mpo* mpo, double dtau, double beta_max,
                       double* beta_reached);
 
+/* Enlarge every bond to about D_target states (each sector scaled by
+ * D_target / D, within what the neighbouring blocks can hold) with zero-weight
+ * orthonormal completions; the state is unchanged, the 1-TDVP manifold larger
+ * (the sweeps then populate the new directions).  Used to reach a large D
+ * without a two-site sweep at that D.  Canonical centre must be on site 0. */
+tt_status tt_rho_pad(tt_rho* rho, const tt_mpo* mpo, int D_target);
+
 /* n_steps 1-TDVP beta-steps of size dtau.  Asynchronous on the ctx stream;
  * the block structure is fixed during the call. */
 tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps);
@@ -162,8 +174,12 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
  * stream and writes *out (host). */
 tt_status tt_measure(tt_rho* rho, const tt_mpo* mpo, tt_obs* out);
 
-/* Statistics of the last tt_tdvp_step call (host *out). */
+/* Statistics accumulated over the tt_tdvp_step calls since the previous
+ * tt_stats_get (host *out; synchronises on the last call's end event). */
 tt_status tt_stats_get(const tt_rho* rho, tt_stats* out);
+/* Profiling mode: record a CUDA event pair around every GEMM / gather launch
+ * of the following tt_tdvp_step calls (on the context stream). */
+tt_status tt_rho_set_profiling(tt_rho* rho, int on);
 
 /* Current bond dimensions: writes N+1 ints (host) to dims. */
 tt_status tt_rho_bond_dims(const tt_rho* rho, int* dims, int n);

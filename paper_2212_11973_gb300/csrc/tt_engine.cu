@@ -373,9 +373,39 @@ struct Eng {
   }
 
   // ---- GEMM / gather dispatch ---------------------------------------------
-  void gemm(const DevGemmBuf& g, const Bases& b, bool use_mixed) {
+  cudaEvent_t prof_begin(int kind, double flops) {
+    if (!r->prof) return nullptr;
+    if (r->evused + 2 > r->evpool.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        r->evpool.push_back(e);
+        r->evkind.push_back(0);
+      }
+    }
+    cudaEvent_t e = r->evpool[r->evused];
+    r->evkind[r->evused] = kind;
+    r->evused += 2;
+    r->kind_flops[kind] += flops;
+    CK(cudaEventRecord(e, st));
+    return e;
+  }
+  void prof_end(cudaEvent_t e) {
+    if (!e) return;
+    CK(cudaEventRecord(r->evpool[r->evused - 1], st));
+  }
+
+  void gemm(const DevGemmBuf& g, const Bases& b, bool use_mixed, int kind = 4) {
+    cudaEvent_t e = prof_begin(kind, g.d.flops);
     if (use_mixed) CK(launch_gemm_bf16(g.d, b, r->nsplit, st));
     else CK(launch_gemm_f64(g.d, b, st));
+    prof_end(e);
+    count();
+  }
+  void gather(const DevGatherBuf& g, const Bases& b, int in, int out) {
+    cudaEvent_t e = prof_begin(3, 0);
+    CK(launch_gather(g.d, b, in, out, st));
+    prof_end(e);
     count();
   }
 
@@ -429,16 +459,16 @@ struct Eng {
       b.p[S_L] = r->Lsp[j].p; b.lo[S_L] = r->Lsize[j];
       b.p[S_R] = r->Rsp[j + 1].p; b.lo[S_R] = r->Rsize[j + 1];
       b.lo[S_T2] = s.h.t2_size;
-      gemm(s.s1, b, true);
-      CK(launch_gather(s.s2.d, b, 1, r->nsplit, st)); count();
-      gemm(s.s3, b, true);
+      gemm(s.s1, b, true, 0);
+      gather(s.s2, b, 1, r->nsplit);
+      gemm(s.s3, b, true, 0);
     } else {
       b.p[S_X] = (void*)x;
       b.p[S_L] = r->L[j].p;
       b.p[S_R] = r->R[j + 1].p;
-      gemm(s.s1, b, false);
-      CK(launch_gather(s.s2.d, b, 0, 0, st)); count();
-      gemm(s.s3, b, false);
+      gemm(s.s1, b, false, 0);
+      gather(s.s2, b, 0, 0);
+      gemm(s.s3, b, false, 0);
     }
     r->heff_flops_acc += s.s1.d.flops + s.s3.d.flops;
     r->step_flops_acc += s.s1.d.flops + s.s3.d.flops;
@@ -468,17 +498,17 @@ struct Eng {
       b.p[S_X] = r->Xs.p; b.lo[S_X] = n;
       b.p[S_L] = r->Lsp[k].p; b.lo[S_L] = r->Lsize[k];
       b.p[S_R] = r->Rsp[k].p; b.lo[S_R] = r->Rsize[k];
-      gemm(bd.b1, b, true);  // T1 in FP64
+      gemm(bd.b1, b, true, 2);  // T1 in FP64
       split((const double*)r->T1.p, bd.h.t_size, r->T2.p);
       b.p[S_T2] = r->T2.p; b.lo[S_T2] = bd.h.t_size;
-      gemm(bd.b2, b, true);
+      gemm(bd.b2, b, true, 2);
     } else {
       b.p[S_X] = (void*)x;
       b.p[S_L] = r->L[k].p;
       b.p[S_R] = r->R[k].p;
       b.p[S_T2] = r->T1.p;
-      gemm(bd.b1, b, false);
-      gemm(bd.b2, b, false);
+      gemm(bd.b1, b, false, 2);
+      gemm(bd.b2, b, false, 2);
     }
     r->step_flops_acc += bd.b1.d.flops + bd.b2.d.flops;
   }
@@ -499,15 +529,15 @@ struct Eng {
       b.p[S_X] = r->Xs.p; b.lo[S_X] = n;
       b.p[S_L] = r->Lsp[j].p; b.lo[S_L] = r->Lsize[j];
       b.lo[S_T2] = s.h.t2_size;
-      gemm(s.s1, b, true);
-      CK(launch_gather(s.s2.d, b, 1, r->nsplit, st)); count();
-      gemm(s.s3l, b, true);
+      gemm(s.s1, b, true, 1);
+      gather(s.s2, b, 1, r->nsplit);
+      gemm(s.s3l, b, true, 1);
     } else {
       b.p[S_X] = r->A[j].p;
       b.p[S_L] = r->L[j].p;
-      gemm(s.s1, b, false);
-      CK(launch_gather(s.s2.d, b, 0, 0, st)); count();
-      gemm(s.s3l, b, false);
+      gemm(s.s1, b, false, 1);
+      gather(s.s2, b, 0, 0);
+      gemm(s.s3l, b, false, 1);
     }
     split_env(r->L, r->Lsp, r->Lsize, j + 1);
     r->step_flops_acc += s.s1.d.flops + s.s3l.d.flops;
@@ -529,15 +559,15 @@ struct Eng {
       b.p[S_X] = r->Xs.p; b.lo[S_X] = n;
       b.p[S_R] = r->Rsp[j + 1].p; b.lo[S_R] = r->Rsize[j + 1];
       b.lo[S_T2] = s.h.u2_size;
-      gemm(s.r1, b, true);
-      CK(launch_gather(s.r2.d, b, 1, r->nsplit, st)); count();
-      gemm(s.r3, b, true);
+      gemm(s.r1, b, true, 1);
+      gather(s.r2, b, 1, r->nsplit);
+      gemm(s.r3, b, true, 1);
     } else {
       b.p[S_X] = r->A[j].p;
       b.p[S_R] = r->R[j + 1].p;
-      gemm(s.r1, b, false);
-      CK(launch_gather(s.r2.d, b, 0, 0, st)); count();
-      gemm(s.r3, b, false);
+      gemm(s.r1, b, false, 1);
+      gather(s.r2, b, 0, 0);
+      gemm(s.r3, b, false, 1);
     }
     split_env(r->R, r->Rsp, r->Rsize, j);
     r->step_flops_acc += s.r1.d.flops + s.r3.d.flops;
@@ -951,6 +981,129 @@ struct Eng {
       r->lay[j + 1] = newn;
       invalidate_bond(j + 1);
     }
+  }
+
+  // Pad every bond to (about) D_target states with zero-weight directions.
+  // Per sector the dimension scales by D_target / D_current (kept within what
+  // both neighbouring site tensors can hold).  With the centre on site 0 and
+  // sites 1..N-1 right-canonical, the new rows of A_k are the orthonormal
+  // completion returned by the Householder QR of [M^T | 0] (M the rows of the
+  // left sector, already orthonormal, so Q starts with M^T), and A_{k-1} gets
+  // zero columns: the state is unchanged, the manifold is larger.
+  void pad_bonds(int D_target) {
+    const int N = r->N;
+    const LocalSpace& ls = M().ls;
+    // targets
+    std::vector<Bond> tgt = r->bond;
+    for (int k = 1; k < N; ++k) {
+      int64_t cur = r->bond[k].total();
+      if (cur >= D_target) continue;
+      double f = (double)D_target / (double)cur;
+      for (size_t q = 0; q < tgt[k].dim.size(); ++q) tgt[k].dim[q] = (int)std::floor(r->bond[k].dim[q] * f);
+    }
+    // feasibility: d'_q <= rows and cols of the neighbouring blocks (iterate)
+    for (int it = 0; it < 4; ++it)
+      for (int k = 1; k < N; ++k)
+        for (int q = 0; q < tgt[k].nsec(); ++q) {
+          int64_t cols = 0, rows = 0;
+          for (int p = 0; p < (int)ls.pq.size(); ++p) {
+            int rr = tgt[k + 1].find(tgt[k].q[q] + ls.pq[p]);
+            if (rr >= 0) cols += (int64_t)ls.pairs[p].size() * tgt[k + 1].dim[rr];
+            int ll = tgt[k - 1].find(tgt[k].q[q] - ls.pq[p]);
+            if (ll >= 0) rows += (int64_t)ls.pairs[p].size() * tgt[k - 1].dim[ll];
+          }
+          int64_t cap = std::min(cols, rows);
+          tgt[k].dim[q] = (int)std::max<int64_t>(r->bond[k].dim[q], std::min<int64_t>(tgt[k].dim[q], cap));
+        }
+    for (int k = N - 1; k >= 1; --k) {
+      const Bond& Bo = r->bond[k];
+      const Bond& Bn = tgt[k];
+      bool same = true;
+      for (int q = 0; q < Bo.nsec(); ++q) same = same && Bo.dim[q] == Bn.dim[q];
+      if (same) continue;
+      const SiteLayout oldk = r->lay[k];
+      const SiteLayout newk = make_site_layout(Bn, r->bond[k + 1], ls);
+      // QR of [M_q^T | 0] per left sector q (cols_q x d'_q, column-major)
+      int64_t ws = 0;
+      std::vector<QrJob> jobs;
+      CopyPlan g, sc;
+      for (int q = 0; q < Bo.nsec(); ++q) {
+        int64_t cols = 0;
+        std::vector<std::pair<int, int64_t>> segs;
+        for (int p = 0; p < oldk.npq; ++p) {
+          int bi = oldk.block_of(q, p);
+          if (bi < 0) continue;
+          segs.push_back({bi, cols});
+          cols += (int64_t)oldk.blk[bi].m * oldk.blk[bi].dr;
+        }
+        QrJob J;
+        J.m = (int)cols;
+        J.n = Bn.dim[q];
+        if (J.n > 2048 || cols < J.n) throw Err{TT_ERR_STATE, "padding target exceeds the sector capacity"};
+        J.a = ws; ws += (int64_t)J.m * J.n;
+        J.q = ws; ws += (int64_t)J.m * J.n;
+        J.r = ws; ws += (int64_t)J.n * J.n;
+        jobs.push_back(J);
+        for (auto& sg : segs) {
+          const SiteBlock& b = oldk.blk[sg.first];
+          const int C = b.m * b.dr;
+          g.items.push_back(CItem{mkref(S_X, b.off), mkref(S_AUX2, J.a + sg.second), C, 1, J.m, 1, b.dl, C});
+          const SiteBlock& nb = newk.blk[newk.block_of(q, b.p)];
+          sc.items.push_back(CItem{mkref(S_AUX2, J.q + sg.second), mkref(S_Y, nb.off), J.m, 1, C, 1, J.n, C});
+        }
+      }
+      check_plan(g, caps({{S_X, oldk.size}, {S_AUX2, ws}}), "pad gather");
+      check_plan(sc, caps({{S_AUX2, ws}, {S_Y, newk.size}}), "pad scatter");
+      // A_{k-1}: zero-padded columns of every right group
+      const SiteLayout oldp = r->lay[k - 1];
+      const SiteLayout newp = make_site_layout(r->bond[k - 1], Bn, ls);
+      CopyPlan zp;
+      for (int q = 0; q < Bo.nsec(); ++q)
+        if (oldp.grp_rows[q] > 0)
+          zp.items.push_back(CItem{mkref(S_X, oldp.grp_off[q]), mkref(S_Y, newp.grp_off[q]), Bo.dim[q], 1, Bn.dim[q], 1,
+                                   (int)oldp.grp_rows[q], Bo.dim[q]});
+      check_plan(zp, caps({{S_X, oldp.size}, {S_Y, newp.size}}), "pad columns");
+      DBuf jb, nA, nP;
+      DevCopyBuf gd, sd, zd;
+      ensure(c, jb, jobs.size() * sizeof(QrJob) + 8);
+      CK(cudaMemcpyAsync(jb.p, jobs.data(), jobs.size() * sizeof(QrJob), cudaMemcpyHostToDevice, st));
+      upload(c, g, gd);
+      upload(c, sc, sd);
+      upload(c, zp, zd);
+      ensure(c, r->ws, (size_t)std::max<int64_t>(ws, 1) * 8);
+      CK(cudaMemsetAsync(r->ws.p, 0, (size_t)std::max<int64_t>(ws, 1) * 8, st));
+      ensure(c, nA, (size_t)newk.size * 8);
+      ensure(c, nP, (size_t)newp.size * 8);
+      CK(cudaMemsetAsync(nA.p, 0, (size_t)newk.size * 8, st));
+      CK(cudaMemsetAsync(nP.p, 0, (size_t)newp.size * 8, st));
+      Bases b{};
+      b.p[S_X] = r->A[k].p;
+      b.p[S_Y] = nA.p;
+      b.p[S_AUX2] = r->ws.p;
+      CK(launch_copy(gd.d, b, st));
+      CK(launch_qr((const QrJob*)jb.p, (int)jobs.size(), dptr(r->ws), st));
+      CK(launch_copy(sd.d, b, st));
+      Bases b2{};
+      b2.p[S_X] = r->A[k - 1].p;
+      b2.p[S_Y] = nP.p;
+      CK(launch_copy(zd.d, b2, st));
+      CK(cudaStreamSynchronize(st));
+      release(c, gd);
+      release(c, sd);
+      release(c, zd);
+      dfree(c, jb);
+      std::swap(r->A[k], nA);
+      std::swap(r->A[k - 1], nP);
+      dfree(c, nA);
+      dfree(c, nP);
+      r->bond[k] = Bn;
+      r->lay[k] = newk;
+      r->lay[k - 1] = newp;
+      invalidate_bond(k);
+    }
+    ensure_vec_capacity();
+    for (int j = N - 1; j >= 1; --j) update_right_env(j);
+    CK(cudaStreamSynchronize(st));
   }
 
   // ---- measurement --------------------------------------------------------------
@@ -1618,6 +1771,7 @@ tt_status tt_rho_create(tt_ctx* ctx, const tt_mpo* mpo, double beta0, int taylor
 void tt_rho_destroy(tt_rho* rho) {
   if (!rho) return;
   cudaStreamSynchronize(rho->ctx->st);
+  for (cudaEvent_t e : rho->evpool) cudaEventDestroy(e);
   if (rho->ev0) cudaEventDestroy(rho->ev0);
   if (rho->ev1) cudaEventDestroy(rho->ev1);
   free_rho(rho);
@@ -1648,9 +1802,14 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
     e.prepare_all();
     if (!rho->ev0) CK(cudaEventCreate(&rho->ev0));
     if (!rho->ev1) CK(cudaEventCreate(&rho->ev1));
-    rho->heff_flops_acc = rho->step_flops_acc = 0;
-    rho->launches_acc = 0;
-    CK(cudaEventRecord(rho->ev0, rho->ctx->st));
+    // statistics accumulate over the calls since the last tt_stats_get
+    if (!rho->stats_pending) {
+      rho->heff_flops_acc = rho->step_flops_acc = 0;
+      rho->launches_acc = 0;
+      rho->evused = 0;
+      for (int k = 0; k < 5; ++k) { rho->kind_ms[k] = 0; rho->kind_n[k] = 0; rho->kind_flops[k] = 0; }
+      CK(cudaEventRecord(rho->ev0, rho->ctx->st));
+    }
     for (int s = 0; s < n_steps; ++s) {
       e.sweep_lr(dtau / 4);
       e.sweep_rl(dtau / 4);
@@ -1683,6 +1842,22 @@ tt_status tt_stats_get(const tt_rho* rho_c, tt_stats* out) {
       return TT_ERR_CUDA;
     }
     rho->stats.step_ms = ms;
+    for (size_t i = 0; i + 1 < rho->evused; i += 2) {
+      float t = 0;
+      if (cudaEventElapsedTime(&t, rho->evpool[i], rho->evpool[i + 1]) != cudaSuccess) {
+        cudaGetLastError();
+        return TT_ERR_CUDA;
+      }
+      rho->kind_ms[rho->evkind[i]] += t;
+      rho->kind_n[rho->evkind[i]] += 1;
+    }
+    rho->stats.heff_ms = rho->kind_ms[0];
+    rho->stats.heff_launches = rho->kind_n[0];
+    rho->stats.env_ms = rho->kind_ms[1];
+    rho->stats.env_flops = rho->kind_flops[1];
+    rho->stats.bond_ms = rho->kind_ms[2];
+    rho->stats.gather_ms = rho->kind_ms[3];
+    rho->stats.gather_launches = rho->kind_n[3];
     rho->stats_pending = false;
   }
   *out = rho->stats;
@@ -1880,6 +2055,20 @@ tt_status tt_rho_load(tt_ctx* ctx, const tt_mpo* mpo, const char* path, const tt
     return s;
   }
   *out = r;
+  return TT_OK;
+}
+
+tt_status tt_rho_pad(tt_rho* rho, const tt_mpo* mpo, int D_target) {
+  if (!rho || mpo != rho->mpo || D_target < 1) return TT_ERR_INVALID_ARG;
+  return guarded(rho->ctx, rho, [&] {
+    Eng e(rho);
+    e.pad_bonds(D_target);
+  });
+}
+
+tt_status tt_rho_set_profiling(tt_rho* rho, int on) {
+  if (!rho) return TT_ERR_INVALID_ARG;
+  rho->prof = on != 0;
   return TT_OK;
 }
 

@@ -130,6 +130,15 @@ struct tt_rho {
   tt_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool stats_pending = false;
+  // per-launch CUDA events (profiling mode): kind 0 = site H_eff GEMMs,
+  // 1 = environment GEMMs, 2 = bond H_eff GEMMs, 3 = gather, 4 = other
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  std::vector<int> evkind;
+  size_t evused = 0;
+  double kind_ms[5] = {0, 0, 0, 0, 0};
+  long long kind_n[5] = {0, 0, 0, 0, 0};
+  double kind_flops[5] = {0, 0, 0, 0, 0};
   double heff_flops_acc = 0, step_flops_acc = 0;
   long long launches_acc = 0;
 };

@@ -7,8 +7,8 @@
 //  * W gather: applies the sparse MPO tensor between the two GEMM stages;
 //  * Lanczos vector kernels in FP64 (Supplement, "Lanczos-based exponential
 //    method"), with deterministic two-stage reductions;
-//  * the small Krylov exponential exp(t T) e_1 by cyclic Jacobi (Golub & Van
-//    Loan, Sec. 8.5) and CUDA's exp();
+//  * the small Krylov exponential exp(t T) e_1 by scaling and squaring of a
+//    Taylor polynomial (Moler & Van Loan);
 //  * Householder QR (FP64) of the per-sector gauge matrices.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -478,57 +478,58 @@ __global__ void beta_finalize(const double* partial, int nblk, int k, int K, dou
   ks->beta[k] = b;
 }
 
-// exp(t T) e_1 for the kdim x kdim tridiagonal T (cyclic Jacobi eigensolver).
-__global__ void krylov_exp_kernel(KrylovState* ks, double t, int K) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int m = ks->kdim;
-  double A[16][16], V[16][16];
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) {
-      A[i][j] = 0.0;
-      V[i][j] = (i == j) ? 1.0 : 0.0;
+// c = exp(t T) e_1 for the kdim x kdim tridiagonal T, by scaling and squaring
+// with a degree-18 Taylor polynomial (Moler & Van Loan, "Nineteen dubious
+// ways", method 3): M = t T / 2^s with ||M||_1 <= 1/4, E = sum_k M^k / k!
+// (Horner), then E <- E^2 s times.  One thread per matrix entry (kdim <= 16).
+__global__ void __launch_bounds__(256) krylov_exp_kernel(KrylovState* ks, double t, int K) {
+  __shared__ double M[16][16], E[16][16], P[16][16];
+  __shared__ int m_s, s_s;
+  const int tid = threadIdx.x, i = tid / 16, j = tid % 16;
+  if (tid == 0) {
+    const int m = ks->kdim;
+    double nrm = 0.0;  // ||t T||_1 (T symmetric tridiagonal)
+    for (int c = 0; c < m; ++c) {
+      double col = fabs(ks->alpha[c]);
+      if (c > 0) col += fabs(ks->beta[c - 1]);
+      if (c + 1 < m) col += fabs(ks->beta[c]);
+      nrm = fmax(nrm, fabs(t) * col);
     }
-  for (int i = 0; i < m; ++i) A[i][i] = ks->alpha[i];
-  for (int i = 0; i + 1 < m; ++i) A[i][i + 1] = A[i + 1][i] = ks->beta[i];
-  for (int sweep = 0; sweep < 64; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) {
-        if (i == j) diag += A[i][i] * A[i][i];
-        else off += A[i][j] * A[i][j];
-      }
-    if (off <= 1e-32 * diag || off == 0.0) break;
-    for (int p = 0; p < m - 1; ++p)
-      for (int q = p + 1; q < m; ++q) {
-        double apq = A[p][q];
-        if (apq == 0.0) continue;
-        double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-        double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
-        double c = 1.0 / sqrt(1.0 + tt * tt), s = tt * c;
-        for (int k = 0; k < m; ++k) {  // A <- A J
-          double akp = A[k][p], akq = A[k][q];
-          A[k][p] = c * akp - s * akq;
-          A[k][q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < m; ++k) {  // A <- J^T A
-          double apk = A[p][k], aqk = A[q][k];
-          A[p][k] = c * apk - s * aqk;
-          A[q][k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < m; ++k) {
-          double vkp = V[k][p], vkq = V[k][q];
-          V[k][p] = c * vkp - s * vkq;
-          V[k][q] = s * vkp + c * vkq;
-        }
-      }
+    int sq = 0;
+    while (nrm > 0.25 && sq < 60) { nrm *= 0.5; ++sq; }
+    m_s = m;
+    s_s = sq;
   }
-  for (int i = 0; i < 17; ++i) ks->c[i] = 0.0;
-  for (int i = 0; i < m; ++i) {
-    double s = 0.0;
-    for (int j = 0; j < m; ++j) s += V[i][j] * exp(t * A[j][j]) * V[0][j];
-    ks->c[i] = s;
+  __syncthreads();
+  const int m = m_s, sq = s_s;
+  const double scale = ldexp(t, -sq);
+  double mij = 0.0;
+  if (i < m && j < m) {
+    if (i == j) mij = ks->alpha[i];
+    else if (j == i + 1) mij = ks->beta[i];
+    else if (i == j + 1) mij = ks->beta[j];
+    mij *= scale;
   }
-  ks->resid = (!ks->broken && m == K) ? ks->nb * ks->beta[K - 1] * fabs(ks->c[K - 1]) : 0.0;
+  M[i][j] = mij;
+  E[i][j] = (i == j && i < m) ? 1.0 : 0.0;  // Horner: E = I + M/18, then E = I + M E / k
+  __syncthreads();
+  for (int k = 18; k >= 1; --k) {
+    double acc = 0.0;
+    for (int q = 0; q < m; ++q) acc = fma(M[i][q], E[q][j], acc);
+    __syncthreads();
+    E[i][j] = (i < m && j < m) ? ((i == j ? 1.0 : 0.0) + acc / (double)k) : 0.0;
+    __syncthreads();
+  }
+  for (int r = 0; r < sq; ++r) {
+    double acc = 0.0;
+    for (int q = 0; q < m; ++q) acc = fma(E[i][q], E[q][j], acc);
+    P[i][j] = acc;
+    __syncthreads();
+    E[i][j] = P[i][j];
+    __syncthreads();
+  }
+  if (tid < 17) ks->c[tid] = (tid < m) ? E[tid][0] : 0.0;
+  if (tid == 0) ks->resid = (!ks->broken && m == K) ? ks->nb * ks->beta[K - 1] * fabs(E[K - 1][0]) : 0.0;
 }
 
 __global__ void __launch_bounds__(VT) combine_kernel(const double* __restrict__ Q, long long ldq,
@@ -822,7 +823,7 @@ cudaError_t k_cgs_pass(const double* Q, int64_t ldq, int k, double* w, int64_t n
 }
 
 cudaError_t k_krylov_exp(KrylovState* ks, double t, int K, cudaStream_t s) {
-  krylov_exp_kernel<<<1, 32, 0, s>>>(ks, t, K);
+  krylov_exp_kernel<<<1, 256, 0, s>>>(ks, t, K);
   return cudaGetLastError();
 }
 

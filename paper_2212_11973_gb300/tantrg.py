@@ -56,10 +56,11 @@ class tt_obs(C.Structure):
 
 
 class tt_stats(C.Structure):
-    _fields_ = [("heff_flops", C.c_double), ("heff_ms", C.c_double), ("step_flops", C.c_double),
-                ("step_ms", C.c_double), ("bytes_lanczos", C.c_double), ("lanczos_ms", C.c_double),
-                ("launches", C.c_longlong), ("n_sites", C.c_int), ("max_bond", C.c_int),
-                ("n_sectors_max", C.c_int)]
+    _fields_ = [("heff_flops", C.c_double), ("heff_ms", C.c_double), ("heff_launches", C.c_longlong),
+                ("env_flops", C.c_double), ("env_ms", C.c_double), ("bond_ms", C.c_double),
+                ("gather_ms", C.c_double), ("gather_launches", C.c_longlong),
+                ("step_flops", C.c_double), ("step_ms", C.c_double), ("launches", C.c_longlong),
+                ("n_sites", C.c_int), ("max_bond", C.c_int), ("n_sectors_max", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,8 +84,10 @@ SIGNATURES = {
     "tt_rho_destroy": (None, [_P]),
     "tt_rho_grow": (C.c_int, [_P, _P, C.c_double, C.c_double, _PD]),
     "tt_tdvp_step": (C.c_int, [_P, _P, C.c_double, C.c_int]),
+    "tt_rho_pad": (C.c_int, [_P, _P, C.c_int]),
     "tt_measure": (C.c_int, [_P, _P, C.POINTER(tt_obs)]),
     "tt_stats_get": (C.c_int, [_P, C.POINTER(tt_stats)]),
+    "tt_rho_set_profiling": (C.c_int, [_P, C.c_int]),
     "tt_rho_bond_dims": (C.c_int, [_P, _PI, C.c_int]),
     "tt_rho_save": (C.c_int, [_P, C.c_char_p]),
     "tt_rho_load": (C.c_int, [_P, _P, C.c_char_p, C.POINTER(tt_run_opts), C.POINTER(_P)]),
@@ -222,6 +225,9 @@ class Rho:
         _check(self.ctx.h, load_library().tt_rho_grow(self.h, self.mpo.h, dtau, beta_max, C.byref(b)))
         return b.value
 
+    def pad(self, D_target):
+        _check(self.ctx.h, load_library().tt_rho_pad(self.h, self.mpo.h, D_target))
+
     def step(self, dtau, n_steps=1):
         _check(self.ctx.h, load_library().tt_tdvp_step(self.h, self.mpo.h, dtau, n_steps))
 
@@ -229,6 +235,9 @@ class Rho:
         o = tt_obs()
         _check(self.ctx.h, load_library().tt_measure(self.h, self.mpo.h, C.byref(o)))
         return o.as_dict()
+
+    def set_profiling(self, on: bool):
+        _check(self.ctx.h, load_library().tt_rho_set_profiling(self.h, int(on)))
 
     def stats(self) -> dict:
         s = tt_stats()

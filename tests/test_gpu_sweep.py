@@ -40,7 +40,7 @@ def _gpu_run(tt, ctx, cfg, beta_end, precision=None, D=None):
     D = D or cfg.D
     prec = cfg.precision if precision is None else precision
     rho = tt.Rho(ctx, mpo, cfg.beta0, tt.run_opts(D, cfg.krylov, prec))
-    rho.grow(cfg.dtau, 1.0)
+    rho.grow(cfg.dtau, min(1.0, beta_end))  # the oracle also stops growing at beta_end
     obs = [rho.measure()]
     while obs[-1]["beta"] < beta_end - 1e-9:
         rho.step(cfg.dtau, 1)
