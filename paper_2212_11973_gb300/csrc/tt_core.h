@@ -80,13 +80,18 @@ SiteLayout make_site_layout(const Bond& L, const Bond& R, const LocalSpace& ls);
 struct EnvLayout {
   std::vector<int64_t> off;     // per ket sector
   std::vector<int64_t> rows;    // per ket sector
+  std::vector<int> ld;          // per ket sector: row stride (d_b, or d_b rounded up to 8)
   std::vector<int64_t> rowoff;  // [b * nw + w] -> first row or -1
   std::vector<int> bra;         // [b * nw + w] -> bra sector or -1
   int nw = 0;
   int64_t size = 0;
   int64_t row_of(int b, int w) const { return rowoff[(size_t)b * nw + w]; }
 };
-EnvLayout make_env_layout(const Bond& B, const std::vector<Q>& chan);
+// pad8: rows padded to a multiple of 8 elements (16-byte aligned bf16 rows,
+// the alignment TMA needs for its global strides and base addresses)
+EnvLayout make_env_layout(const Bond& B, const std::vector<Q>& chan, bool pad8 = false);
+inline int pad8i(int x) { return (x + 7) / 8 * 8; }
+inline int64_t pad8l(int64_t x) { return (x + 7) / 8 * 8; }
 
 // Block-diagonal bond matrix (sector q -> q), row-major d_q x d_q blocks.
 struct BondMatLayout {
@@ -185,6 +190,7 @@ struct CItem {
   int64_t src_rs, src_cs, dst_rs, dst_cs;
   int rows, cols;
 };
+// FP64 -> split-bf16 copy (levels at dst + l * lo[slot(dst)]) uses CItem too.
 struct CopyPlan {
   std::vector<CItem> items;
 };

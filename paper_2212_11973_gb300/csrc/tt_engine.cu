@@ -21,6 +21,8 @@
 #include <new>
 #include <numeric>
 
+#include <cudaTypedefs.h>
+
 #include "tt_engine.h"
 
 using namespace tt;
@@ -104,6 +106,9 @@ void upload(tt_ctx* c, const GemmPlan& p, DevGemmBuf& o) {
   o.d.flops = p.flops;
   o.host = p;
   o.checked = false;
+  o.tc_checked = o.tc_ok = false;
+  o.ntiles128 = 0;
+  for (int i = 0; i < 8; ++i) { o.key_p[i] = nullptr; o.key_lo[i] = 0; }
 }
 
 void upload(tt_ctx* c, const GatherPlan& p, DevGatherBuf& o) {
@@ -132,7 +137,16 @@ void upload(tt_ctx* c, const CopyPlan& p, DevCopyBuf& o) {
   o.checked = false;
 }
 
-void release(tt_ctx* c, DevGemmBuf& o) { dfree(c, o.buf); o.d = DevGemm(); o.host = GemmPlan(); o.checked = false; }
+void release(tt_ctx* c, DevGemmBuf& o) {
+  dfree(c, o.buf);
+  dfree(c, o.maps);
+  dfree(c, o.tiles128);
+  o.d = DevGemm();
+  o.host = GemmPlan();
+  o.checked = o.tc_checked = o.tc_ok = false;
+  o.ntiles128 = 0;
+  for (int i = 0; i < 8; ++i) { o.key_p[i] = nullptr; o.key_lo[i] = 0; }
+}
 void release(tt_ctx* c, DevGatherBuf& o) { dfree(c, o.buf); o.d = DevGather(); o.host = GatherPlan(); o.checked = false; }
 void release(tt_ctx* c, DevCopyBuf& o) { dfree(c, o.buf); o.d = DevCopy(); o.host = CopyPlan(); o.checked = false; }
 
@@ -218,6 +232,7 @@ struct Eng {
     if (k - 1 >= 0) { r->sp[k - 1].valid = false; r->qrl[k - 1].valid = false; r->lqr[k - 1].valid = false; r->meas[k - 1].valid = false; }
     if (k < r->N) { r->sp[k].valid = false; r->qrl[k].valid = false; r->lqr[k].valid = false; r->meas[k].valid = false; }
     r->bp[k].valid = false;
+    r->esplit_ok[k] = 0;
     for (int j = std::max(0, k - 2); j <= std::min(r->N - 1, k + 1); ++j) { r->absl_ok[j] = 0; r->absr_ok[j] = 0; }
   }
 
@@ -249,7 +264,7 @@ struct Eng {
       ensure(c, r->Qk, (size_t)cap * r->opts.krylov_dim * sizeof(double));
       ensure(c, r->W, (size_t)cap * sizeof(double));
       ensure(c, r->tmp, (size_t)cap * sizeof(double));
-      ensure(c, r->Xs, (size_t)cap * 3 * 2);
+      ensure(c, r->Xn, (size_t)cap * 3 * 2);
     }
   }
 
@@ -261,7 +276,9 @@ struct Eng {
     if (s.valid) return s;
     const Mpo& m = M();
     s.h = build_site_plan(r->bond[j], r->bond[j + 1], m.ls, m.site[j].terms, m.chan[j], m.chan[j + 1], mixed());
-    validate_site(s.h, r->bond[j], r->bond[j + 1], m.chan[j], m.chan[j + 1]);
+    validate_site(s.h, r->bond[j], r->bond[j + 1], m.chan[j], m.chan[j + 1], mixed());
+    upload(c, s.h.xsplit, s.xs);
+    if (mixed()) ensure(c, r->Xs, (size_t)std::max<int64_t>(s.h.xt_size, 1) * 2 * r->nsplit);
     upload(c, s.h.s1, s.s1);
     upload(c, s.h.s2, s.s2);
     upload(c, s.h.s3, s.s3);
@@ -278,23 +295,26 @@ struct Eng {
   }
 
   static void validate_site(const SitePlanHost& h, const Bond& BL, const Bond& BR, const std::vector<Q>& chl,
-                            const std::vector<Q>& chr) {
+                            const std::vector<Q>& chr, bool mx) {
     const int64_t n = h.lay.size, el = make_env_layout(BL, chl).size, er = make_env_layout(BR, chr).size;
-    check_plan(h.s1, caps({{S_X, n}, {S_L, el}, {S_T1, h.t1_size}}), "S1");
+    const int64_t elo = make_env_layout(BL, chl, mx).size, ero = make_env_layout(BR, chr, mx).size;
+    const int sx = mx ? S_AUX : S_X;  // natural-layout x operand
+    check_plan(h.s1, caps({{S_X, mx ? h.xt_size : n}, {S_L, elo}, {S_T1, h.t1_size}}), "S1");
     check_plan(h.s2, caps({{S_T1, h.t1_size}, {S_T2, h.t2_size}}), "S2");
-    check_plan(h.s3, caps({{S_T2, h.t2_size}, {S_R, er}, {S_Y, n}}), "S3");
-    check_plan(h.s3l, caps({{S_X, n}, {S_T2, h.t2_size}, {S_Y, er}}), "S3L");
-    check_plan(h.r1, caps({{S_X, n}, {S_R, er}, {S_T1, h.u1_size}}), "R1");
+    check_plan(h.s3, caps({{S_T2, h.t2_size}, {S_R, ero}, {S_Y, n}}), "S3");
+    check_plan(h.s3l, caps({{sx, n}, {S_T2, h.t2_size}, {S_Y, er}}), "S3L");
+    check_plan(h.r1, caps({{sx, n}, {S_R, ero}, {S_T1, h.u1_size}}), "R1");
     check_plan(h.r2, caps({{S_T1, h.u1_size}, {S_T2, h.u2_size}}), "R2");
-    check_plan(h.r3, caps({{S_X, n}, {S_T2, h.u2_size}, {S_Y, el}}), "R3");
+    check_plan(h.r3, caps({{sx, n}, {S_T2, h.u2_size}, {S_Y, el}}), "R3");
+    if (mx) check_plan(h.xsplit, caps({{S_X, n}, {S_Y, h.xt_size}}), "x split");
   }
 
   BondDev& bond_plan(int k) {
     BondDev& b = r->bp[k];
     if (b.valid) return b;
-    b.h = build_bond_plan(r->bond[k], M().chan[k]);
+    b.h = build_bond_plan(r->bond[k], M().chan[k], mixed());
     {
-      int64_t e = make_env_layout(r->bond[k], M().chan[k]).size;
+      int64_t e = make_env_layout(r->bond[k], M().chan[k], mixed()).size;
       check_plan(b.h.b1, caps({{S_X, b.h.mat.size}, {S_L, e}, {S_T1, b.h.t_size}}), "B1");
       check_plan(b.h.b2, caps({{S_T2, b.h.t_size}, {S_R, e}, {S_Y, b.h.mat.size}}), "B2");
     }
@@ -395,10 +415,96 @@ struct Eng {
     CK(cudaEventRecord(r->evpool[r->evused - 1], st));
   }
 
-  void gemm(const DevGemmBuf& g, const Bases& b, bool use_mixed, int kind = 4) {
+  // tcgen05 eligibility (K-major A and B, 16-byte aligned rows and offsets) and
+  // the per-segment tensor maps for the current slot bases.
+  bool prep_tc(DevGemmBuf& g, const Bases& b) {
+    if (!g.tc_checked) {
+      g.tc_checked = true;
+      g.tc_ok = !g.host.segs.empty();
+      for (const GSeg& sg : g.host.segs) {
+        const int64_t oa = (int64_t)(sg.A & 0x00FFFFFFFFFFFFFFull), ob = (int64_t)(sg.B & 0x00FFFFFFFFFFFFFFull);
+        if (sg.tA != 0 || sg.tB != 1 || sg.lda % 8 || sg.ldb % 8 || oa % 8 || ob % 8) g.tc_ok = false;
+      }
+      if (!g.tc_ok) return false;
+      std::vector<GTile> tiles;
+      for (size_t gi = 0; gi < g.host.groups.size(); ++gi) {
+        const GGroup& gg = g.host.groups[gi];
+        for (int m0 = 0; m0 < gg.M; m0 += 128)
+          for (int n0 = 0; n0 < gg.N; n0 += 128) tiles.push_back(GTile{(int)gi, m0, n0, 0});
+      }
+      ensure(c, g.tiles128, tiles.size() * sizeof(GTile) + 16);
+      if (!tiles.empty())
+        CK(cudaMemcpyAsync(g.tiles128.p, tiles.data(), tiles.size() * sizeof(GTile), cudaMemcpyHostToDevice, st));
+      g.ntiles128 = (int)tiles.size();
+    }
+    if (!g.tc_ok) return false;
+    bool same = true;
+    for (int i = 0; i < 8; ++i) same = same && g.key_p[i] == b.p[i] && g.key_lo[i] == b.lo[i];
+    if (same && g.maps.p) return true;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+      cudaDriverEntryPointQueryResult q;
+      void* fn = nullptr;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+          !fn) {
+        cudaGetLastError();
+        g.tc_ok = false;
+        return false;
+      }
+      encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const size_t nseg = g.host.segs.size();
+    std::vector<CUtensorMap> maps(2 * nseg);
+    std::vector<int> seg_group(nseg, 0);
+    for (size_t gi = 0; gi < g.host.groups.size(); ++gi)
+      for (int si = g.host.groups[gi].seg0; si < g.host.groups[gi].seg1; ++si) seg_group[si] = (int)gi;
+    for (size_t si = 0; si < nseg; ++si) {
+      const GSeg& sg = g.host.segs[si];
+      const GGroup& gg = g.host.groups[seg_group[si]];
+      for (int w = 0; w < 2; ++w) {
+        const Ref ref = w == 0 ? sg.A : sg.B;
+        const int sl = (int)(ref >> 56);
+        const int64_t off = (int64_t)(ref & 0x00FFFFFFFFFFFFFFull);
+        const long long lo = b.lo[sl];
+        if (!b.p[sl] || lo % 8 || sg.K < 1) { g.tc_ok = false; return false; }
+        cuuint64_t dims[3] = {(cuuint64_t)sg.K, (cuuint64_t)std::max(1, w == 0 ? gg.M : gg.N), (cuuint64_t)r->nsplit};
+        cuuint64_t strides[2] = {(cuuint64_t)(w == 0 ? sg.lda : sg.ldb) * 2, (cuuint64_t)lo * 2};
+        cuuint32_t box[3] = {64, 128, 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        void* base = (char*)b.p[sl] + off * 2;
+        CUresult cr = encode(&maps[2 * si + w], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) {
+          if (std::getenv("TT_DEBUG"))
+            std::fprintf(stderr, "[tc] tensor map encode failed (%d) seg %zu K %d ld %d lo %lld\n", (int)cr, si, sg.K,
+                         w == 0 ? sg.lda : sg.ldb, lo);
+          g.tc_ok = false;
+          return false;
+        }
+      }
+    }
+    ensure(c, g.maps, maps.size() * sizeof(CUtensorMap) + 128);
+    CK(cudaMemcpyAsync(g.maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < 8; ++i) { g.key_p[i] = b.p[i]; g.key_lo[i] = b.lo[i]; }
+    return true;
+  }
+
+  void gemm(DevGemmBuf& g, const Bases& b, bool use_mixed, int kind = 4) {
     cudaEvent_t e = prof_begin(kind, g.d.flops);
-    if (use_mixed) CK(launch_gemm_bf16(g.d, b, r->nsplit, st));
-    else CK(launch_gemm_f64(g.d, b, st));
+    if (use_mixed && r->use_tc && kind == 0 && prep_tc(g, b)) {
+      if (!r->tcerr.p) {
+        ensure(c, r->tcerr, 16);
+        CK(cudaMemsetAsync(r->tcerr.p, 0, 16, st));
+      }
+      CK(launch_gemm_tc(g.d.groups, g.d.segs, (const GTile*)g.tiles128.p, g.ntiles128, g.maps.p, b, r->nsplit,
+                        (int*)r->tcerr.p, st));
+    } else if (use_mixed) {
+      CK(launch_gemm_bf16(g.d, b, r->nsplit, st));
+    } else {
+      CK(launch_gemm_f64(g.d, b, st));
+    }
     prof_end(e);
     count();
   }
@@ -417,12 +523,37 @@ struct Eng {
   // environment buffers
   void ensure_env(std::vector<DBuf>& v, std::vector<DBuf>& vsp, std::vector<int64_t>& sz, int k) {
     int64_t n = make_env_layout(r->bond[k], M().chan[k]).size;
+    int64_t np = make_env_layout(r->bond[k], M().chan[k], true).size;
     sz[k] = n;
+    (&sz == &r->Lsize ? r->Lpsize : r->Rpsize)[k] = np;
     ensure(c, v[k], (size_t)n * 8);
-    if (mixed()) ensure(c, vsp[k], (size_t)n * 2 * r->nsplit);
+    if (mixed()) ensure(c, vsp[k], (size_t)std::max<int64_t>(np, 1) * 2 * r->nsplit);
   }
+  // FP64 environment -> split-bf16 copy with rows padded to 8 elements
   void split_env(std::vector<DBuf>& v, std::vector<DBuf>& vsp, std::vector<int64_t>& sz, int k) {
-    if (mixed()) split((const double*)v[k].p, sz[k], vsp[k].p);
+    if (!mixed()) return;
+    if (!r->esplit_ok[k]) {
+      CopyPlan cp = build_env_split(r->bond[k], M().chan[k]);
+      check_plan(cp, caps({{S_X, make_env_layout(r->bond[k], M().chan[k]).size},
+                           {S_Y, make_env_layout(r->bond[k], M().chan[k], true).size}}), "env split");
+      upload(c, cp, r->esplit[k]);
+      r->esplit_ok[k] = 1;
+    }
+    Bases b{};
+    b.p[S_X] = v[k].p;
+    b.p[S_Y] = vsp[k].p;
+    b.lo[S_Y] = (&sz == &r->Lsize ? r->Lpsize : r->Rpsize)[k];
+    CK(launch_split_copy(r->esplit[k].d, b, r->nsplit, st));
+    count();
+  }
+  // x -> transposed padded split copy for S1's B operand (Xs)
+  void split_x_transposed(SiteDev& s, const double* x) {
+    Bases b{};
+    b.p[S_X] = (void*)x;
+    b.p[S_Y] = r->Xs.p;
+    b.lo[S_Y] = s.h.xt_size;
+    CK(launch_split_copy(s.xs.d, b, r->nsplit, st));
+    count();
   }
 
   static void need(const DBuf& b, int64_t bytes, const char* what) {
@@ -432,14 +563,15 @@ struct Eng {
   }
   void need_site(int j, const SiteDev& s, bool left_env_in, bool right_env_in) {
     const int el = mixed() ? 2 * r->nsplit : 8;
-    if (left_env_in) { need(r->L[j], r->Lsize[j] * 8, "L"); if (mixed()) need(r->Lsp[j], r->Lsize[j] * el, "Lsp"); }
-    if (right_env_in) { need(r->R[j + 1], r->Rsize[j + 1] * 8, "R"); if (mixed()) need(r->Rsp[j + 1], r->Rsize[j + 1] * el, "Rsp"); }
+    if (left_env_in) { need(r->L[j], r->Lsize[j] * 8, "L"); if (mixed()) need(r->Lsp[j], r->Lpsize[j] * el, "Lsp"); }
+    if (right_env_in) { need(r->R[j + 1], r->Rsize[j + 1] * 8, "R"); if (mixed()) need(r->Rsp[j + 1], r->Rpsize[j + 1] * el, "Rsp"); }
+    if (mixed()) need(r->Xs, std::max<int64_t>(s.h.xt_size, 1) * 2 * r->nsplit, "Xs");
     if (left_env_in && r->Lsize[j] != make_env_layout(r->bond[j], M().chan[j]).size) throw Err{TT_ERR_STATE, "stale L"};
     if (right_env_in && r->Rsize[j + 1] != make_env_layout(r->bond[j + 1], M().chan[j + 1]).size) throw Err{TT_ERR_STATE, "stale R"};
     need(r->T1, std::max(s.h.t1_size, s.h.u1_size) * 8, "T1");
     need(r->T2, std::max(s.h.t2_size, s.h.u2_size) * 8, "T2");
     need(r->W, s.h.lay.size * 8, "W");
-    need(r->Xs, s.h.lay.size * 2 * std::max(r->nsplit, 1), "Xs");
+    need(r->Xn, s.h.lay.size * 2 * std::max(r->nsplit, 1), "Xn");
     if (r->ldq < s.h.lay.size) throw Err{TT_ERR_STATE, "Krylov capacity"};
   }
 
@@ -453,11 +585,10 @@ struct Eng {
     b.p[S_T1] = r->T1.p;
     b.p[S_T2] = r->T2.p;
     if (mixed() && !force_fp64) {
-      int64_t n = s.h.lay.size;
-      split(x, n, r->Xs.p);
-      b.p[S_X] = r->Xs.p; b.lo[S_X] = n;
-      b.p[S_L] = r->Lsp[j].p; b.lo[S_L] = r->Lsize[j];
-      b.p[S_R] = r->Rsp[j + 1].p; b.lo[S_R] = r->Rsize[j + 1];
+      split_x_transposed(s, x);
+      b.p[S_X] = r->Xs.p; b.lo[S_X] = s.h.xt_size;
+      b.p[S_L] = r->Lsp[j].p; b.lo[S_L] = r->Lpsize[j];
+      b.p[S_R] = r->Rsp[j + 1].p; b.lo[S_R] = r->Rpsize[j + 1];
       b.lo[S_T2] = s.h.t2_size;
       gemm(s.s1, b, true, 0);
       gather(s.s2, b, 1, r->nsplit);
@@ -483,21 +614,21 @@ struct Eng {
       if (r->Lsize[k] != e || r->Rsize[k] != e) throw Err{TT_ERR_STATE, "stale bond environments"};
       need(r->L[k], e * 8, "L");
       need(r->R[k], e * 8, "R");
-      if (mixed()) { need(r->Lsp[k], e * el, "Lsp"); need(r->Rsp[k], e * el, "Rsp"); }
+      if (mixed()) { need(r->Lsp[k], r->Lpsize[k] * el, "Lsp"); need(r->Rsp[k], r->Rpsize[k] * el, "Rsp"); }
       need(r->T1, bd.h.t_size * 8, "T1");
       need(r->T2, bd.h.t_size * el, "T2");
       need(r->W, bd.h.mat.size * 8, "W");
-      need(r->Xs, bd.h.mat.size * 2 * std::max(r->nsplit, 1), "Xs");
+      need(r->Xn, bd.h.mat.size * 2 * std::max(r->nsplit, 1), "Xn");
     }
     Bases b{};
     b.p[S_Y] = y;
     b.p[S_T1] = r->T1.p;
     if (mixed()) {
       int64_t n = bd.h.mat.size;
-      split(x, n, r->Xs.p);
-      b.p[S_X] = r->Xs.p; b.lo[S_X] = n;
-      b.p[S_L] = r->Lsp[k].p; b.lo[S_L] = r->Lsize[k];
-      b.p[S_R] = r->Rsp[k].p; b.lo[S_R] = r->Rsize[k];
+      split(x, n, r->Xn.p);
+      b.p[S_X] = r->Xn.p; b.lo[S_X] = n;
+      b.p[S_L] = r->Lsp[k].p; b.lo[S_L] = r->Lpsize[k];
+      b.p[S_R] = r->Rsp[k].p; b.lo[S_R] = r->Rpsize[k];
       gemm(bd.b1, b, true, 2);  // T1 in FP64
       split((const double*)r->T1.p, bd.h.t_size, r->T2.p);
       b.p[S_T2] = r->T2.p; b.lo[S_T2] = bd.h.t_size;
@@ -525,9 +656,11 @@ struct Eng {
     b.p[S_T2] = r->T2.p;
     if (mixed()) {
       int64_t n = s.h.lay.size;
-      split(dptr(r->A[j]), n, r->Xs.p);
-      b.p[S_X] = r->Xs.p; b.lo[S_X] = n;
-      b.p[S_L] = r->Lsp[j].p; b.lo[S_L] = r->Lsize[j];
+      split_x_transposed(s, dptr(r->A[j]));
+      split(dptr(r->A[j]), n, r->Xn.p);
+      b.p[S_X] = r->Xs.p; b.lo[S_X] = s.h.xt_size;
+      b.p[S_AUX] = r->Xn.p; b.lo[S_AUX] = n;
+      b.p[S_L] = r->Lsp[j].p; b.lo[S_L] = r->Lpsize[j];
       b.lo[S_T2] = s.h.t2_size;
       gemm(s.s1, b, true, 1);
       gather(s.s2, b, 1, r->nsplit);
@@ -555,9 +688,9 @@ struct Eng {
     b.p[S_T2] = r->T2.p;
     if (mixed()) {
       int64_t n = s.h.lay.size;
-      split(dptr(r->A[j]), n, r->Xs.p);
-      b.p[S_X] = r->Xs.p; b.lo[S_X] = n;
-      b.p[S_R] = r->Rsp[j + 1].p; b.lo[S_R] = r->Rsize[j + 1];
+      split(dptr(r->A[j]), n, r->Xn.p);
+      b.p[S_AUX] = r->Xn.p; b.lo[S_AUX] = n;
+      b.p[S_R] = r->Rsp[j + 1].p; b.lo[S_R] = r->Rpsize[j + 1];
       b.lo[S_T2] = s.h.u2_size;
       gemm(s.r1, b, true, 1);
       gather(s.r2, b, 1, r->nsplit);
@@ -1194,6 +1327,7 @@ struct Eng {
     CK(cudaStreamSynchronize(st));
     dfree(c, part2);
     if (rs.bad) throw Err{TT_ERR_NUMERIC, "non-finite or zero norm in a Krylov update"};
+    check_tc();
     double nrm2 = hv[3];
     out->beta = r->beta;
     out->energy_per_site = hv[2] / nrm2 / N;
@@ -1492,12 +1626,15 @@ struct Eng {
     const Mpo& m = M();
     MpoSite w12 = combine_two_sites(m, j, r->mpo->ls2);
     SitePlanHost h = build_site_plan(r->bond[j], r->bond[j + 2], r->mpo->ls2, w12.terms, m.chan[j], m.chan[j + 2], mixed());
-    validate_site(h, r->bond[j], r->bond[j + 2], m.chan[j], m.chan[j + 2]);
+    validate_site(h, r->bond[j], r->bond[j + 2], m.chan[j], m.chan[j + 2], mixed());
     DevGemmBuf s1, s3;
     DevGatherBuf s2;
+    DevCopyBuf xs;
     upload(c, h.s1, s1);
     upload(c, h.s2, s2);
     upload(c, h.s3, s3);
+    upload(c, h.xsplit, xs);
+    if (mixed()) ensure(c, r->Xs, (size_t)std::max<int64_t>(h.xt_size, 1) * 2 * r->nsplit);
     ensure(c, r->T1, (size_t)std::max<int64_t>(h.t1_size, 1) * 8);
     ensure(c, r->T2, (size_t)std::max<int64_t>(h.t2_size, 1) * 8);
     int64_t n = C2.size;
@@ -1506,7 +1643,7 @@ struct Eng {
       ensure(c, r->Qk, (size_t)r->ldq * r->opts.krylov_dim * 8);
       ensure(c, r->W, (size_t)r->ldq * 8);
       ensure(c, r->tmp, (size_t)r->ldq * 8);
-      ensure(c, r->Xs, (size_t)r->ldq * 3 * 2);
+      ensure(c, r->Xn, (size_t)r->ldq * 3 * 2);
     }
     auto apply = [&](const double* x, double* y) {
       Bases b{};
@@ -1514,10 +1651,14 @@ struct Eng {
       b.p[S_T1] = r->T1.p;
       b.p[S_T2] = r->T2.p;
       if (mixed()) {
-        split(x, n, r->Xs.p);
-        b.p[S_X] = r->Xs.p; b.lo[S_X] = n;
-        b.p[S_L] = r->Lsp[j].p; b.lo[S_L] = r->Lsize[j];
-        b.p[S_R] = r->Rsp[j + 2].p; b.lo[S_R] = r->Rsize[j + 2];
+        Bases bx{};
+        bx.p[S_X] = (void*)x;
+        bx.p[S_Y] = r->Xs.p;
+        bx.lo[S_Y] = h.xt_size;
+        CK(launch_split_copy(xs.d, bx, r->nsplit, st));
+        b.p[S_X] = r->Xs.p; b.lo[S_X] = h.xt_size;
+        b.p[S_L] = r->Lsp[j].p; b.lo[S_L] = r->Lpsize[j];
+        b.p[S_R] = r->Rsp[j + 2].p; b.lo[S_R] = r->Rpsize[j + 2];
         b.lo[S_T2] = h.t2_size;
         CK(launch_gemm_bf16(s1.d, b, r->nsplit, st));
         CK(launch_gather(s2.d, b, 1, r->nsplit, st));
@@ -1536,6 +1677,7 @@ struct Eng {
     release(c, s1);
     release(c, s2);
     release(c, s3);
+    release(c, xs);
   }
 
   void grow_sweep_lr(double tau) {
@@ -1582,6 +1724,14 @@ struct Eng {
     CK(cudaMemcpyAsync(&rs, r->rs.p, sizeof(rs), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (rs.bad) throw Err{TT_ERR_NUMERIC, "non-finite or zero norm in a Krylov update"};
+    check_tc();
+  }
+  void check_tc() {
+    if (!r->tcerr.p) return;
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, r->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (e) throw Err{TT_ERR_TIMEOUT, "a bounded mbarrier wait of the tcgen05 GEMM expired"};
   }
 };
 
@@ -1620,6 +1770,14 @@ void alloc_rho_arrays(tt_rho* r) {
   r->Rsp.assign(N + 1, DBuf());
   r->Lsize.assign(N + 1, 0);
   r->Rsize.assign(N + 1, 0);
+  r->Lpsize.assign(N + 1, 0);
+  r->Rpsize.assign(N + 1, 0);
+  r->esplit.assign(N + 1, DevCopyBuf());
+  r->esplit_ok.assign(N + 1, 0);
+  {
+    const char* gk = std::getenv("TT_GEMM_KERNEL");
+    r->use_tc = !(gk && std::strcmp(gk, "mma") == 0);
+  }
   r->sp.assign(N, SiteDev());
   r->bp.assign(N + 1, BondDev());
   r->qrl.assign(N, QrDev());
@@ -1641,14 +1799,18 @@ void free_rho(tt_rho* r) {
   for (auto& b : r->A) dfree(c, b);
   for (auto* v : {&r->L, &r->R, &r->Lsp, &r->Rsp})
     for (auto& b : *v) dfree(c, b);
-  for (auto& s : r->sp) { release(c, s.s1); release(c, s.s2); release(c, s.s3); release(c, s.s3l); release(c, s.r1); release(c, s.r2); release(c, s.r3); }
+  for (auto& s : r->sp) {
+    release(c, s.s1); release(c, s.s2); release(c, s.s3); release(c, s.s3l); release(c, s.r1); release(c, s.r2);
+    release(c, s.r3); release(c, s.xs);
+  }
+  for (auto& e : r->esplit) release(c, e);
   for (auto& s : r->bp) { release(c, s.b1); release(c, s.b2); }
   for (auto* v : {&r->qrl, &r->lqr})
     for (auto& q : *v) { dfree(c, q.jobs); release(c, q.gather); release(c, q.scatter); release(c, q.rout); }
   for (auto& g : r->absl) release(c, g);
   for (auto& g : r->absr) release(c, g);
   for (auto& m : r->meas) { release(c, m.t); release(c, m.el); dfree(c, m.items); }
-  for (DBuf* b : {&r->Qk, &r->W, &r->Xs, &r->T1, &r->T2, &r->Sb, &r->ws, &r->partial, &r->ks, &r->rs, &r->tmp, &r->obs, &r->el0, &r->el1})
+  for (DBuf* b : {&r->Qk, &r->W, &r->Xs, &r->Xn, &r->T1, &r->T2, &r->Sb, &r->ws, &r->partial, &r->ks, &r->rs, &r->tmp, &r->obs, &r->el0, &r->el1, &r->tcerr})
     dfree(c, *b);
 }
 

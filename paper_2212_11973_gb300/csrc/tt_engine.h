@@ -46,8 +46,14 @@ void check_cuda(cudaError_t e, const char* what);
 struct DevGemmBuf {
   DevGemm d;
   DBuf buf;
-  GemmPlan host;       // kept for the bounds check before the first launch
+  GemmPlan host;       // kept for the bounds check and the tensor maps
   bool checked = false;
+  // tcgen05 path: eligibility, 128 x 128 tile list, per-segment tensor maps
+  bool tc_checked = false, tc_ok = false;
+  DBuf maps, tiles128;
+  int ntiles128 = 0;
+  void* key_p[8] = {nullptr};
+  long long key_lo[8] = {0};
 };
 struct DevGatherBuf {
   DevGather d;
@@ -84,6 +90,7 @@ struct SiteDev {
   SitePlanHost h;
   DevGemmBuf s1, s3, s3l, r1, r3;
   DevGatherBuf s2, r2;
+  DevCopyBuf xs;  // split-bf16 mode: x -> transposed padded copy (S1's B operand)
 };
 struct BondDev {
   bool valid = false;
@@ -118,14 +125,18 @@ struct tt_rho {
   std::vector<tt::SiteLayout> lay;      // N
   std::vector<tt::DBuf> A;              // N site tensors (FP64)
   std::vector<tt::DBuf> L, R, Lsp, Rsp; // environments (FP64) and split copies
-  std::vector<int64_t> Lsize, Rsize;
+  std::vector<int64_t> Lsize, Rsize;      // FP64 environment sizes (elements)
+  std::vector<int64_t> Lpsize, Rpsize;    // split-bf16 copies: rows padded to 8 (elements per level)
+  std::vector<tt::DevCopyBuf> esplit;     // per bond: FP64 environment -> padded split copy
+  std::vector<char> esplit_ok;
+  bool use_tc = true;                     // tcgen05 kernel for eligible split-bf16 GEMMs
   std::vector<tt::SiteDev> sp;
   std::vector<tt::BondDev> bp;
   std::vector<tt::QrDev> qrl, lqr;
   std::vector<tt::DevGemmBuf> absl, absr;
   std::vector<char> absl_ok, absr_ok;
   std::vector<tt::MeasDev> meas;
-  tt::DBuf Qk, W, Xs, T1, T2, Sb, ws, partial, ks, rs, tmp, obs, el0, el1;
+  tt::DBuf Qk, W, Xs, Xn, T1, T2, Sb, ws, partial, ks, rs, tmp, obs, el0, el1, tcerr;
   int64_t ldq = 0;
   tt_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -303,6 +303,28 @@ __global__ void __launch_bounds__(256) copy_kernel(const CItem* __restrict__ ite
   }
 }
 
+// Strided FP64 -> split-bf16 copy: levels at dst + l * lo[slot(dst)].
+template <int NS>
+__global__ void __launch_bounds__(256) split_copy_kernel(const CItem* __restrict__ items, Bases bs) {
+  const CItem it = items[blockIdx.x];
+  const double* src = rptr<const double>(bs, it.src);
+  __nv_bfloat16* dst = rptr<__nv_bfloat16>(bs, it.dst);
+  const long long lo = bs.lo[slot_of(it.dst)];
+  const long long total = (long long)it.rows * it.cols;
+  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
+    long long r, c;
+    if (it.dst_cs == 1) { r = e / it.cols; c = e % it.cols; } else { c = e / it.rows; r = e % it.rows; }
+    double rem = src[r * it.src_rs + c * it.src_cs];
+    const long long o = r * it.dst_rs + c * it.dst_cs;
+#pragma unroll
+    for (int l = 0; l < NS; ++l) {
+      const __nv_bfloat16 h = __double2bfloat16(rem);
+      dst[l * lo + o] = h;
+      rem -= (double)__bfloat162float(h);
+    }
+  }
+}
+
 // x (FP64, n) -> ns bf16 levels out[l * n + i], x ~ sum_l out[l]
 __global__ void split_bf16_kernel(const double* __restrict__ x, long long n, int ns, __nv_bfloat16* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -784,6 +806,14 @@ cudaError_t launch_split_bf16(const double* x, int64_t n, int nsplit, void* out,
 }
 
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) { return cudaMemsetAsync(p, 0, bytes, s); }
+
+cudaError_t launch_split_copy(const DevCopy& c, const Bases& b, int nsplit, cudaStream_t s) {
+  if (c.nitems == 0) return cudaSuccess;
+  if (nsplit == 2) split_copy_kernel<2><<<c.nitems, 256, 0, s>>>(c.items, b);
+  else if (nsplit == 3) split_copy_kernel<3><<<c.nitems, 256, 0, s>>>(c.items, b);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
 
 cudaError_t k_norm_init(const double* v, int64_t n, double* partial, KrylovState* ks, double* q0, cudaStream_t s) {
   int g = grid_for(n);

@@ -67,6 +67,13 @@ cudaError_t launch_gather(const DevGather& g, const Bases& b, int in_type, int o
 cudaError_t launch_copy(const DevCopy& c, const Bases& b, cudaStream_t s);
 cudaError_t launch_split_bf16(const double* x, int64_t n, int nsplit, void* out /* bf16[nsplit*n] */, cudaStream_t s);
 cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
+// strided FP64 -> split-bf16 copy (levels at dst + l * lo[slot(dst)])
+cudaError_t launch_split_copy(const DevCopy& c, const Bases& b, int nsplit, cudaStream_t s);
+// tcgen05 grouped GEMM (tt_tcgen05.cu): K-major A and B, 128 x 128 tiles,
+// maps = 2 CUtensorMap (A, B) per segment in global memory.
+size_t tc_smem_bytes(int nsplit);
+cudaError_t launch_gemm_tc(const GGroup* groups, const GSeg* segs, const GTile* tiles128, int ntiles,
+                           const void* maps, const Bases& b, int nsplit, int* err, cudaStream_t s);
 
 // Lanczos exponential steps on flat FP64 vectors of length n.  Q holds the
 // Krylov basis with leading dimension ldq.  `partial` is scratch of

@@ -94,11 +94,12 @@ SiteLayout make_site_layout(const Bond& L, const Bond& R, const LocalSpace& ls) 
   return S;
 }
 
-EnvLayout make_env_layout(const Bond& B, const std::vector<Q>& chan) {
+EnvLayout make_env_layout(const Bond& B, const std::vector<Q>& chan, bool pad8) {
   EnvLayout E;
   E.nw = (int)chan.size();
   E.off.assign(B.nsec(), 0);
   E.rows.assign(B.nsec(), 0);
+  E.ld.assign(B.nsec(), 0);
   E.rowoff.assign((size_t)B.nsec() * E.nw, -1);
   E.bra.assign((size_t)B.nsec() * E.nw, -1);
   int64_t off = 0;
@@ -113,7 +114,8 @@ EnvLayout make_env_layout(const Bond& B, const std::vector<Q>& chan) {
       row += B.dim[a];
     }
     E.rows[b] = row;
-    off += row * B.dim[b];
+    E.ld[b] = pad8 ? pad8i(B.dim[b]) : B.dim[b];
+    off += row * E.ld[b];
   }
   E.size = off;
   return E;

@@ -41,14 +41,29 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
   const SiteLayout& S = P.lay;
   EnvLayout EL = make_env_layout(BL, chl);
   EnvLayout ER = make_env_layout(BR, chr);
+  // operand layouts of the contraction inputs: split-bf16 environments have
+  // rows padded to 8 elements; FP64 ones are the natural layout
+  EnvLayout ELo = make_env_layout(BL, chl, mixed);
+  EnvLayout ERo = make_env_layout(BR, chr, mixed);
+  auto wpad = [&](int x) { return mixed ? pad8i(x) : x; };
   const int nwl = (int)chl.size(), nwr = (int)chr.size();
   const int t1flag = mixed ? 2 : 0;
   TermIndex ti(terms);
   const int d = ls.d;
 
-  // ---- S1
-  std::vector<int64_t> t1off(S.blk.size(), -1), t1ld(S.blk.size(), 0);
-  int64_t cur = 0;
+  // ---- S1 (mixed: B = transposed x block [(s, a_r)][a_l], rows padded: K-major)
+  std::vector<int64_t> t1off(S.blk.size(), -1), t1ld(S.blk.size(), 0), xtoff(S.blk.size(), 0);
+  int64_t cur = 0, xt = 0;
+  if (mixed)
+    for (size_t bi = 0; bi < S.blk.size(); ++bi) {
+      const SiteBlock& b = S.blk[bi];
+      const int N = b.m * b.dr, ldt = pad8i(b.dl);
+      xtoff[bi] = xt;
+      // x block row-major (d_l x N) -> transposed (N x ldt)
+      P.xsplit.items.push_back(CItem{mkref(S_X, b.off), mkref(S_Y, xt), N, 1, 1, ldt, b.dl, N});
+      xt += (int64_t)N * ldt;
+    }
+  P.xt_size = pad8l(xt);
   for (size_t bi = 0; bi < S.blk.size(); ++bi) {
     const SiteBlock& b = S.blk[bi];
     int64_t M = EL.rows[b.l];
@@ -57,7 +72,8 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
     t1off[bi] = cur;
     t1ld[bi] = N;
     P.s1.add_group((int)M, (int)N, mkref(S_T1, cur), (int)N, t1flag);
-    P.s1.add_seg(mkref(S_L, EL.off[b.l]), b.dl, 0, mkref(S_X, b.off), (int)N, 0, b.dl);
+    if (mixed) P.s1.add_seg(mkref(S_L, ELo.off[b.l]), ELo.ld[b.l], 0, mkref(S_X, xtoff[bi]), pad8i(b.dl), 1, b.dl);
+    else P.s1.add_seg(mkref(S_L, EL.off[b.l]), b.dl, 0, mkref(S_X, b.off), (int)N, 0, b.dl);
     cur += M * N;
   }
   P.t1_size = cur;
@@ -74,7 +90,7 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
       if (b < 0) continue;
       t2col[(size_t)r * nwr + w] = cols;
       t2ket[(size_t)r * nwr + w] = b;
-      cols += BR.dim[b];
+      cols += wpad(BR.dim[b]);
     }
     t2cols[r] = cols;
     t2off[r] = cur;
@@ -133,8 +149,8 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
         if (col < 0) continue;
         const int b = t2ket[(size_t)r * nwr + w2];
         int64_t rrow = ER.row_of(b, w2);
-        P.s3.add_seg(mkref(S_T2, t2off[r] + col), (int)t2cols[r], 0, mkref(S_R, ER.off[b] + rrow * BR.dim[b]),
-                     BR.dim[b], 1, BR.dim[b]);
+        P.s3.add_seg(mkref(S_T2, t2off[r] + col), (int)t2cols[r], 0, mkref(S_R, ERo.off[b] + rrow * ERo.ld[b]),
+                     ERo.ld[b], 1, BR.dim[b]);
       }
     }
     for (int w2 = 0; w2 < nwr; ++w2) {
@@ -144,8 +160,8 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
       int64_t lrow = ER.row_of(b, w2);
       P.s3l.add_group(BR.dim[r], BR.dim[b], mkref(S_Y, ER.off[b] + lrow * BR.dim[b]), BR.dim[b], 0);
       if (S.grp_rows[r] > 0)
-        P.s3l.add_seg(mkref(S_X, S.grp_off[r]), BR.dim[r], 1, mkref(S_T2, t2off[r] + col), (int)t2cols[r], 0,
-                      (int)S.grp_rows[r]);
+        P.s3l.add_seg(mkref(mixed ? S_AUX : S_X, S.grp_off[r]), BR.dim[r], 1, mkref(S_T2, t2off[r] + col),
+                      (int)t2cols[r], 0, (int)S.grp_rows[r]);
     }
   }
   P.lenv_size = ER.size;
@@ -161,7 +177,7 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
     u1off[bi] = cur;
     u1ld[bi] = N;
     P.r1.add_group((int)M, (int)N, mkref(S_T1, cur), (int)N, t1flag);
-    P.r1.add_seg(mkref(S_X, b.off), b.dr, 0, mkref(S_R, ER.off[b.r]), b.dr, 1, b.dr);
+    P.r1.add_seg(mkref(mixed ? S_AUX : S_X, b.off), b.dr, 0, mkref(S_R, ERo.off[b.r]), ERo.ld[b.r], 1, b.dr);
     cur += M * N;
   }
   P.u1_size = cur;
@@ -251,7 +267,7 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
         if (obi < 0) continue;
         const SiteBlock& ob = S.blk[obi];
         int K = ob.m * ob.dr;
-        P.r3.add_seg(mkref(S_X, ob.off), K, 0,
+        P.r3.add_seg(mkref(mixed ? S_AUX : S_X, ob.off), K, 0,
                      mkref(S_T2, u2off[a] + row0 * u2cols[a] + colseg[(size_t)a * S.npq + p]), (int)u2cols[a], 1, K);
       }
     }
@@ -259,9 +275,19 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
   return P;
 }
 
-BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch) {
+CopyPlan build_env_split(const Bond& B, const std::vector<Q>& chan) {
+  EnvLayout E = make_env_layout(B, chan), P = make_env_layout(B, chan, true);
+  CopyPlan cp;
+  for (int b = 0; b < B.nsec(); ++b)
+    if (E.rows[b] > 0)
+      cp.items.push_back(CItem{mkref(S_X, E.off[b]), mkref(S_Y, P.off[b]), E.ld[b], 1, P.ld[b], 1, (int)E.rows[b], B.dim[b]});
+  return cp;
+}
+
+BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed) {
   BondPlanHost P;
   EnvLayout E = make_env_layout(B, ch);
+  EnvLayout Eo = make_env_layout(B, ch, mixed);  // operand layout of L and R
   P.mat = make_bondmat_layout(B);
   const int nw = (int)ch.size();
   std::vector<int64_t> toff(B.nsec(), -1);
@@ -270,7 +296,7 @@ BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch) {
     if (E.rows[b] == 0) continue;
     toff[b] = cur;
     P.b1.add_group((int)E.rows[b], B.dim[b], mkref(S_T1, cur), B.dim[b], 0);
-    P.b1.add_seg(mkref(S_L, E.off[b]), B.dim[b], 0, mkref(S_X, P.mat.off[b]), B.dim[b], 0, B.dim[b]);
+    P.b1.add_seg(mkref(S_L, Eo.off[b]), Eo.ld[b], 0, mkref(S_X, P.mat.off[b]), B.dim[b], 0, B.dim[b]);
     cur += E.rows[b] * B.dim[b];
   }
   P.t_size = cur;
@@ -280,8 +306,8 @@ BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch) {
       int b = B.find(B.q[q] - ch[w]);
       if (b < 0 || toff[b] < 0) continue;
       int64_t row = E.row_of(b, w);
-      P.b2.add_seg(mkref(S_T2, toff[b] + row * B.dim[b]), B.dim[b], 0, mkref(S_R, E.off[b] + row * B.dim[b]),
-                   B.dim[b], 1, B.dim[b]);
+      P.b2.add_seg(mkref(S_T2, toff[b] + row * B.dim[b]), B.dim[b], 0, mkref(S_R, Eo.off[b] + row * Eo.ld[b]),
+                   Eo.ld[b], 1, B.dim[b]);
     }
   }
   return P;

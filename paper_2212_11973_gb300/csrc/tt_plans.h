@@ -10,7 +10,13 @@ struct SitePlanHost {
   GatherPlan s2, r2;
   int64_t t1_size = 0, t2_size = 0, u1_size = 0, u2_size = 0;
   int64_t lenv_size = 0, renv_size = 0;
+  // split-bf16 mode: S1 reads x as per-block transposed copies [(s, a_r)][a_l]
+  // with rows padded to 8 elements (K-major B operand); xsplit copies x there.
+  CopyPlan xsplit;
+  int64_t xt_size = 0;
 };
+// FP64 environment (natural layout) -> split-bf16 copy with rows padded to 8.
+CopyPlan build_env_split(const Bond& B, const std::vector<Q>& chan);
 
 struct BondPlanHost {
   BondMatLayout mat;
@@ -29,7 +35,7 @@ struct QrPlanHost {
 
 SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& ls, const std::vector<MpoTerm>& terms,
                              const std::vector<Q>& chl, const std::vector<Q>& chr, bool mixed);
-BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch);
+BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed);
 GemmPlan build_absorb_left(const SiteLayout& oldl, const SiteLayout& newl, const Bond& Bold, const Bond& Bnew,
                            const std::vector<int64_t>& soff, const std::vector<int>& new_of_old);
 GemmPlan build_absorb_right(const SiteLayout& oldl, const SiteLayout& newl, const Bond& Bold, const Bond& Bnew,

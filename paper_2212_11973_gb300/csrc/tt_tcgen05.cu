@@ -1,0 +1,353 @@
+// Split-BF16 grouped GEMM on the 5th-generation tensor cores (sm_103a).
+//
+// One CTA computes a 128 x 128 output tile of one group: for every segment of
+// the group and every 64-wide K chunk, TMA loads the NS bf16 levels of the A
+// tile (128 rows x 64 K) and of the B tile (128 rows x 64 K, K-major) into
+// 128B-swizzled shared memory, one elected thread issues tcgen05.mma
+// (kind::f16, bf16 x bf16 -> f32, M = 128, N = 128, K = 16) for the level
+// products l_A + l_B < NS into a TMEM accumulator, and every FOLD chunks all
+// 128 threads read the accumulator back (tcgen05.ld) and add it into a
+// two-float (hi, lo) sum kept in TMEM (TwoSum, Knuth TAOCP 4.2.2), so the FP32
+// accumulation error does not grow with K.  The epilogue writes hi + lo as
+// FP32 or FP64.  Two shared-memory stages overlap the TMA of chunk c+1 with the
+// MMAs of chunk c.  Every mbarrier wait is bounded: on expiry the CTA records
+// an error code, drains its own copies in flight, frees its TMEM and returns.
+//
+// Both operands must be K-major (A stored M x K, B stored N x K, K contiguous)
+// with leading dimensions and offsets that are multiples of 8 elements; the
+// host checks this before choosing the kernel.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tt_kernels.h"
+
+namespace tt {
+
+namespace {
+
+constexpr int TBM = 128, TBN = 128, TBK = 64;
+constexpr int TILE_BYTES = TBM * TBK * 2;  // 16 KB per level and operand
+constexpr int FOLD = 2;                    // chunks per TMEM fold
+constexpr uint32_t TMEM_COLS = 512;        // acc [0,128), hi [128,256), lo [256,384)
+constexpr long long WAIT_LIMIT = 1ll << 26;
+
+__device__ __forceinline__ int slot_of(Ref r) { return (int)(r >> 56); }
+__device__ __forceinline__ long long off_of(Ref r) { return (long long)(r & 0x00FFFFFFFFFFFFFFull); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false when the limit expired
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version
+  d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
+      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])),
+      "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
+      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])),
+      "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])),
+      "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])),
+      "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int NS>
+__global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restrict__ groups,
+                                                         const GSeg* __restrict__ segs,
+                                                         const GTile* __restrict__ tiles,
+                                                         const CUtensorMap* __restrict__ maps, Bases bs,
+                                                         int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], acc_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  constexpr int NPROD = NS == 2 ? 3 : 6;
+  constexpr int STAGE_BYTES = 2 * NS * TILE_BYTES;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const GTile tl = tiles[blockIdx.x];
+  const GGroup g = groups[tl.g];
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&full_bar[0], 1);
+    mbar_init(&full_bar[1], 1);
+    mbar_init(&empty_bar[0], 1);
+    mbar_init(&empty_bar[1], 1);
+    mbar_init(&acc_bar, 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_s;
+  const uint32_t t_acc = tmem, t_hi = tmem + TBN, t_lo = tmem + 2 * TBN;
+  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+
+  // instruction descriptor: D f32, A/B bf16, both K-major, N = 128, M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) | ((uint32_t)(TBM >> 4) << 24);
+
+  // chunk bookkeeping (thread 0 walks the segments)
+  int total = 0;
+  for (int si = g.seg0; si < g.seg1; ++si) total += (segs[si].K + TBK - 1) / TBK;
+
+  int cur_seg = g.seg0, cur_k = 0, fenced_seg = -1;  // producer cursor
+  auto issue_tma = [&](int c) {
+    // advance cursor to chunk c (chunks are issued in order)
+    while (cur_seg < g.seg1 && cur_k >= segs[cur_seg].K) { ++cur_seg; cur_k = 0; }
+    const int s = c & 1;
+    uint8_t* st = smem + s * STAGE_BYTES;
+    const CUtensorMap* ma = maps + 2 * cur_seg;
+    const CUtensorMap* mb = maps + 2 * cur_seg + 1;
+    if (fenced_seg != cur_seg) {  // tensor maps written by a host copy: acquire before first use
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma)) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb)) : "memory");
+      fenced_seg = cur_seg;
+    }
+    mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+#pragma unroll
+    for (int l = 0; l < NS; ++l) tma_load_3d(st + l * TILE_BYTES, ma, cur_k, tl.m0, l, &full_bar[s]);
+#pragma unroll
+    for (int l = 0; l < NS; ++l) tma_load_3d(st + (NS + l) * TILE_BYTES, mb, cur_k, tl.n0, l, &full_bar[s]);
+    cur_k += TBK;
+  };
+
+  int issued = 0;   // TMA chunks issued
+  int folds = 0;
+  bool ok = true;
+  float v[32], h[32], w[32];
+  for (int b0 = 0; b0 < total; b0 += FOLD) {
+    const int b1 = min(total, b0 + FOLD);
+    if (tid == 0) {
+      for (int c = b0; c < b1 && ok; ++c) {
+        if (issued == c) { issue_tma(c); ++issued; }
+        if (c + 1 < total && issued == c + 1) {
+          if (c + 1 >= 2) ok = ok && mbar_wait(&empty_bar[(c + 1) & 1], ((c - 1) >> 1) & 1);
+          if (ok) { issue_tma(c + 1); ++issued; }
+        }
+        if (!ok) break;
+        const int s = c & 1;
+        ok = mbar_wait(&full_bar[s], (c >> 1) & 1);
+        if (!ok) break;
+        fence_after();
+        const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+        for (int p = 0; p < NPROD; ++p) {
+          const int la = (p == 2 || p == 4) ? 1 : (p == 5 ? 2 : 0);
+          const int lb = (p == 1 || p == 4) ? 1 : (p == 3 ? 2 : 0);
+          const uint32_t aa = sa + la * TILE_BYTES, ba = sa + (NS + lb) * TILE_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < TBK / 16; ++kk) {
+            const uint32_t acc = (c > b0 || p > 0 || kk > 0) ? 1u : 0u;
+            umma_f16(t_acc, make_desc(aa + kk * 32), make_desc(ba + kk * 32), idesc, acc);
+          }
+        }
+        umma_commit(&empty_bar[s]);
+      }
+      if (ok) umma_commit(&acc_bar);
+      else abort_s = 1;
+    }
+    __syncthreads();
+    if (abort_s) break;
+    if (!mbar_wait(&acc_bar, folds & 1)) {
+      abort_s = 1;
+      break;
+    }
+    fence_after();
+#pragma unroll 1
+    for (int cb = 0; cb < TBN; cb += 32) {
+      tmem_ld32(t_acc + lane_off + cb, v);
+      if (folds == 0) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) w[i] = 0.f;
+        tmem_st32(t_hi + lane_off + cb, v);
+        tmem_st32(t_lo + lane_off + cb, w);
+      } else {
+        tmem_ld32(t_hi + lane_off + cb, h);
+        tmem_ld32(t_lo + lane_off + cb, w);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float s = h[i] + v[i];
+          const float bp = s - h[i];
+          const float ap = s - bp;
+          w[i] += (h[i] - ap) + (v[i] - bp);
+          h[i] = s;
+        }
+        tmem_st32(t_hi + lane_off + cb, h);
+        tmem_st32(t_lo + lane_off + cb, w);
+      }
+    }
+    ++folds;
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
+
+  if (abort_s) {
+    // drain the copies this CTA may still have in flight, then give up
+    if (tid == 0) {
+      if (err) atomicExch(err, 1);
+      for (int c = 0; c < issued; ++c) mbar_wait(&full_bar[c & 1], (c >> 1) & 1);
+    }
+    __syncthreads();
+  } else {
+    // epilogue: row = tid
+    const int row = tl.m0 + tid;
+    const bool accum = g.flags & 1, out_f32 = g.flags & 2;
+#pragma unroll 1
+    for (int cb = 0; cb < TBN; cb += 32) {
+      if (folds > 0) {
+        tmem_ld32(t_hi + lane_off + cb, h);
+        tmem_ld32(t_lo + lane_off + cb, w);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) { h[i] = 0.f; w[i] = 0.f; }
+      }
+      if (row < g.M) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = tl.n0 + cb + i;
+          if (col < g.N) {
+            const double val = (double)h[i] + (double)w[i];
+            const long long o = (long long)row * g.ldc + col;
+            if (out_f32) {
+              float* C = reinterpret_cast<float*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+              *C = accum ? *C + (float)val : (float)val;
+            } else {
+              double* C = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+              *C = accum ? *C + val : val;
+            }
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+}  // namespace
+
+size_t tc_smem_bytes(int nsplit) { return (size_t)2 * 2 * nsplit * TILE_BYTES + 1024; }
+
+cudaError_t launch_gemm_tc(const GGroup* groups, const GSeg* segs, const GTile* tiles128, int ntiles,
+                           const void* maps, const Bases& b, int nsplit, int* err, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  const size_t smem = tc_smem_bytes(nsplit);
+  if (nsplit == 2) {
+    static bool set2 = false;
+    if (!set2) {
+      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      set2 = true;
+    }
+    gemm_tc_kernel<2><<<ntiles, 128, smem, s>>>(groups, segs, tiles128, (const CUtensorMap*)maps, b, err);
+  } else if (nsplit == 3) {
+    static bool set3 = false;
+    if (!set3) {
+      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      set3 = true;
+    }
+    gemm_tc_kernel<3><<<ntiles, 128, smem, s>>>(groups, segs, tiles128, (const CUtensorMap*)maps, b, err);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace tt

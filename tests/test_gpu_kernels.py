@@ -1,0 +1,49 @@
+"""GPU kernel-level parity: one site H_eff apply on seeded random block-sparse
+inputs (ladder MPO, Gaussian sector dimensions), split-BF16 paths against the
+FP64 path of the same library call.  The FP64 apply itself is pinned to the
+oracle by the sweep parity tests; here the tolerances are the split-BF16
+error bounds: ~2^-16 relative for 2 levels, ~2^-24 times a small factor for 3
+levels (the FP32 accumulation is folded into a two-float sum per K chunk, so
+it does not grow with K)."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2212_11973_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+ALLOWED = [(n, s) for n in range(-4, 5) for s in range(-4, 5) if (n + s) % 2 == 0]
+
+
+@pytest.fixture(scope="module")
+def tt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2212_11973_gb300 import tantrg
+    tantrg.load_library()
+    return tantrg
+
+
+def _inputs(tt, mpo, site, D, seed):
+    SL = wl.gaussian_sectors(D, 1.5, ALLOWED, seed)
+    SR = wl.gaussian_sectors(D, 1.5, ALLOWED, seed + 1)
+    nx, nl, nr = tt.layout_sizes(mpo, site, SL, SR)
+    return SL, SR, wl.random_vector(nl, seed + 2), wl.random_vector(nr, seed + 3), wl.random_vector(nx, seed + 4)
+
+
+@pytest.mark.parametrize("D", [24, 130, 300])
+def test_heff_split_bf16_matches_fp64(tt, D):
+    ctx = tt.Context()
+    mpo = tt.Mpo(ctx, 8, 2, False, t=1.0, U=4.0, mu=-0.3, form=1)
+    SL, SR, L, R, x = _inputs(tt, mpo, 7, D, 11 * D)
+    y0 = tt.heff_apply_host(ctx, mpo, 7, 0, SL, SR, L, R, x)
+    assert np.isfinite(y0).all() and np.abs(y0).max() > 0
+    for prec, tol in ((1, 3e-5), (2, 1e-6)):
+        y = tt.heff_apply_host(ctx, mpo, 7, prec, SL, SR, L, R, x)
+        err = np.linalg.norm(y - y0) / np.linalg.norm(y0)
+        assert err < tol, (D, prec, err)
+    mpo.close()
+    ctx.close()
