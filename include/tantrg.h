@@ -219,6 +219,14 @@ tt_status tt_heff_apply_host(tt_ctx* ctx, const tt_mpo* mpo, int site, int preci
                              const int* nsec_lr, const int* qn, const int* qs, const int* qd,
                              const double* L, const double* R, const double* x, double* y);
 
+/* QR gauge kernel on one matrix (Supplement, "Procedure of 1-TDVP", step 3:
+ * A_i = A_i^L S_i by QR): A = Q R for a column-major m x n matrix (ld = m,
+ * 1 <= n <= min(m, 2048)), Householder in FP64, sign convention diag(R) >= 0.
+ * A, Q (m x n, column-major) and R (n x n, column-major, upper triangular) are
+ * device pointers; A is not modified.  Scratch comes from the context
+ * allocator.  Synchronises the context stream. */
+tt_status tt_qr_device(tt_ctx* ctx, const double* A, int m, int n, double* Q, double* R);
+
 #ifdef __cplusplus
 }
 #endif

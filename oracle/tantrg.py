@@ -135,29 +135,26 @@ def lanczos_expm(apply, v, t, K):
 # Gauge moves
 # ----------------------------------------------------------------------------
 
-def _signfix(R):
+def qr_signfixed(M):
+    """Reduced QR M = Q R of an m x n matrix with the convention diag(R) >= 0
+    (unique for full column rank)."""
+    Q, R = np.linalg.qr(M)
     d = np.sign(np.diag(R))
     d[d == 0] = 1.0
-    return d
+    return Q * d[None, :], d[:, None] * R
 
 
 def qr_left(A):
     """A = A^L S with A^L left-canonical (QR of the (D_l*16) x D_r matrix)."""
     Dl, _, _, Dr = A.shape
-    Q, R = np.linalg.qr(A.reshape(Dl * 16, Dr))
-    d = _signfix(R)
-    Q = Q * d[None, :]
-    R = d[:, None] * R
+    Q, R = qr_signfixed(A.reshape(Dl * 16, Dr))
     return Q.reshape(Dl, 4, 4, Q.shape[1]), R
 
 
 def lq_right(A):
     """A = S A^R with A^R right-canonical (QR of the transposed D_l x (16*D_r) matrix)."""
     Dl, _, _, Dr = A.shape
-    Q, R = np.linalg.qr(A.reshape(Dl, 16 * Dr).T)
-    d = _signfix(R)
-    Q = Q * d[None, :]
-    R = d[:, None] * R
+    Q, R = qr_signfixed(A.reshape(Dl, 16 * Dr).T)
     return Q.T.reshape(Q.shape[1], 4, 4, Dr), R.T
 
 

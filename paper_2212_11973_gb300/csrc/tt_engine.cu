@@ -2234,4 +2234,27 @@ tt_status tt_rho_set_profiling(tt_rho* rho, int on) {
   return TT_OK;
 }
 
+tt_status tt_qr_device(tt_ctx* ctx, const double* A, int m, int n, double* Q, double* R) {
+  if (!ctx || !A || !Q || !R || m < 1 || n < 1 || n > 2048 || m < n) {
+    if (ctx) ctx->err = "tt_qr_device: need device pointers and 1 <= n <= min(m, 2048)";
+    return TT_ERR_INVALID_ARG;
+  }
+  DBuf ws, job;
+  tt_status st = guarded(ctx, nullptr, [&] {
+    const int64_t mn = (int64_t)m * n;
+    ensure(ctx, ws, (size_t)(2 * mn + (int64_t)n * n) * sizeof(double));
+    ensure(ctx, job, sizeof(QrJob));
+    QrJob J{0, mn, 2 * mn, m, n};
+    CK(cudaMemcpyAsync(job.p, &J, sizeof(J), cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ws.p, A, mn * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(launch_qr((const QrJob*)job.p, 1, (double*)ws.p, ctx->st));
+    CK(cudaMemcpyAsync(Q, (double*)ws.p + mn, mn * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(R, (double*)ws.p + 2 * mn, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+  });
+  dfree(ctx, ws);
+  dfree(ctx, job);
+  return st;
+}
+
 }  // extern "C"

@@ -93,6 +93,7 @@ SIGNATURES = {
     "tt_rho_load": (C.c_int, [_P, _P, C.c_char_p, C.POINTER(tt_run_opts), C.POINTER(_P)]),
     "tt_layout_sizes": (C.c_int, [_P, C.c_int, _PI, _PI, _PI, _PI, _PL, _PL, _PL]),
     "tt_heff_apply_host": (C.c_int, [_P, _P, C.c_int, C.c_int, _PI, _PI, _PI, _PI, _PD, _PD, _PD, _PD]),
+    "tt_qr_device": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
 }
 
 _lib = None
@@ -297,3 +298,17 @@ def heff_apply_host(ctx: Context, mpo: Mpo, site, precision, sectors_l, sectors_
     _check(ctx.h, load_library().tt_heff_apply_host(ctx.h, mpo.h, site, precision, nsec, qn, qs, qd,
                                                      pd(L), pd(R), pd(x), pd(y)))
     return y
+
+
+def qr_device(ctx: Context, A):
+    """A = Q R on the device (FP64 Householder, diag(R) >= 0).  A: torch CUDA
+    float64 tensor (m, n), m >= n.  Returns (Q, R) as torch tensors."""
+    import torch
+    m, n = A.shape
+    At = A.t().contiguous()  # column-major m x n
+    Q = torch.empty((n, m), dtype=torch.float64, device=A.device)
+    R = torch.empty((n, n), dtype=torch.float64, device=A.device)
+    _check(ctx.h, load_library().tt_qr_device(ctx.h, C.c_void_p(At.data_ptr()), m, n, C.c_void_p(Q.data_ptr()),
+                                              C.c_void_p(R.data_ptr())))
+    return Q.t(), R.t()
+

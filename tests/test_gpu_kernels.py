@@ -47,3 +47,20 @@ def test_heff_split_bf16_matches_fp64(tt, D):
         assert err < tol, (D, prec, err)
     mpo.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (40, 7), (300, 130), (2100, 200)])
+def test_qr_gauge_matches_oracle(tt, m, n):
+    """QR gauge kernel (FP64 Householder, diag(R) >= 0) against the oracle's QR."""
+    import torch
+    from oracle.tantrg import qr_signfixed
+    ctx = tt.Context()
+    A = wl.random_vector(m * n, 100 + m).reshape(m, n)
+    Qo, Ro = qr_signfixed(A)
+    Q, R = tt.qr_device(ctx, torch.from_numpy(A).cuda())
+    Q, R = Q.cpu().numpy(), R.cpu().numpy()
+    scale = np.abs(A).max()
+    assert np.abs(Q - Qo).max() < 1e-12 * max(1.0, np.linalg.cond(A))
+    assert np.abs(R - Ro).max() < 1e-12 * scale * max(1.0, np.linalg.cond(A))
+    assert np.abs(Q.T @ Q - np.eye(n)).max() < 1e-13
+    ctx.close()
