@@ -227,6 +227,24 @@ tt_status tt_heff_apply_host(tt_ctx* ctx, const tt_mpo* mpo, int site, int preci
  * allocator.  Synchronises the context stream. */
 tt_status tt_qr_device(tt_ctx* ctx, const double* A, int m, int n, double* Q, double* R);
 
+/* The same QR without any device allocation, for callers that may not allocate
+ * device memory at that point (a memory pool that must not grow, an allocator
+ * owned by another framework, a latency-bound path where cudaMalloc could
+ * synchronise).  The paper has no counterpart; this is a library service.
+ *   Scratch: a fixed 16 MiB array in device global memory, reserved on every GPU
+ *   that loads the library until the process exits.  Limit: 8 + 2 m n + n^2
+ *   doubles (e.g. m = 2048, n = 448); larger sizes, or n > 2048, or m < n return
+ *   TT_ERR_INVALID_ARG without touching the GPU.
+ *   A (m x n, column-major), Q (m x n, column-major) and R (n x n, column-major)
+ *   are device pointers of the current device; the work is queued on
+ *   cuda_stream (NULL: legacy default stream) and the call returns without
+ *   synchronising.  The first call on a device looks up the scratch address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.  Every call on a device shares the one scratch
+ *   array and it keeps the last call's contents: calls that overlap on the GPU
+ *   (different streams, no ordering) race and corrupt each other. */
+tt_status tt_qr_device_noalloc(const double* A, int m, int n, double* Q, double* R, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

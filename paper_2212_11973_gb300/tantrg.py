@@ -94,6 +94,7 @@ SIGNATURES = {
     "tt_layout_sizes": (C.c_int, [_P, C.c_int, _PI, _PI, _PI, _PI, _PL, _PL, _PL]),
     "tt_heff_apply_host": (C.c_int, [_P, _P, C.c_int, C.c_int, _PI, _PI, _PI, _PI, _PD, _PD, _PD, _PD]),
     "tt_qr_device": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
+    "tt_qr_device_noalloc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
 }
 
 _lib = None
@@ -312,3 +313,15 @@ def qr_device(ctx: Context, A):
                                               C.c_void_p(R.data_ptr())))
     return Q.t(), R.t()
 
+
+def qr_device_noalloc(A, Q, R, stream=None):
+    """tt_qr_device_noalloc on caller-provided torch CUDA float64 buffers:
+    A (n, m) holds the column-major m x n input, Q (n, m) and R (n, n) receive
+    the column-major factors.  Allocates nothing; queued on `stream`."""
+    import torch
+    n, m = A.shape
+    st = (stream or torch.cuda.current_stream()).cuda_stream
+    status = load_library().tt_qr_device_noalloc(C.c_void_p(A.data_ptr()), m, n, C.c_void_p(Q.data_ptr()),
+                                                 C.c_void_p(R.data_ptr()), C.c_void_p(st))
+    if status != TT_OK:
+        raise TTError(status, "tt_qr_device_noalloc failed (sizes beyond the fixed scratch, or a CUDA error)")
