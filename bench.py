@@ -276,6 +276,7 @@ def main():
         "heff_tflops": heff_tflops, "env_tflops": (env_fl / (env_ms / 1e3) / 1e12) if env_ms > 0 else None,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 56,
                 "includes": "tt_tdvp_step + tt_measure (measurement sweep and observables to host)"},
+        "breakdown_ms_per_step": {k: s[k + "_ms"] / args.steps for k in ("heff", "env", "qr", "bond", "gather")},
         "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
         "observables": {k: obs[k] for k in ("beta", "energy_per_site", "density", "double_occ",
                                             "free_energy_per_site")} if obs else None,

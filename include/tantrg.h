@@ -125,6 +125,9 @@ typedef struct {
   double step_ms;          /* device time of the last tt_tdvp_step call (events) */
   long long launches;      /* kernels launched by the last tt_tdvp_step call */
   int n_sites, max_bond, n_sectors_max;
+  double qr_ms;            /* QR gauge factorisations: CholeskyQR3 GEMMs and
+                              Cholesky kernels plus the Householder fallback
+                              (profiling mode) */
 } tt_stats;
 
 /* ---- context ---------------------------------------------------------- */

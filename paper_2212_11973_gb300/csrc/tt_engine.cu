@@ -227,7 +227,15 @@ struct Eng {
   void count(int n = 1) { r->launches_acc += n; }
 
   // ---- structure ----------------------------------------------------------
+  void drop_graph() {
+    if (r->graph) {
+      cudaGraphExecDestroy(r->graph);
+      r->graph = nullptr;
+    }
+  }
+
   void invalidate_bond(int k) {
+    drop_graph();
     // plans touching bond k
     if (k - 1 >= 0) { r->sp[k - 1].valid = false; r->qrl[k - 1].valid = false; r->lqr[k - 1].valid = false; r->meas[k - 1].valid = false; }
     if (k < r->N) { r->sp[k].valid = false; r->qrl[k].valid = false; r->lqr[k].valid = false; r->meas[k].valid = false; }
@@ -244,6 +252,7 @@ struct Eng {
   void set_precision(int prec) {
     const int ns = prec <= 0 ? 0 : (prec == 1 ? 2 : 3);
     if (ns == r->nsplit) return;
+    drop_graph();
     r->nsplit = ns;
     for (auto& sp : r->sp) sp.valid = false;
     for (auto& bp : r->bp) bp.valid = false;
@@ -361,7 +370,32 @@ struct Eng {
     upload(c, q.h.gather, q.gather);
     upload(c, q.h.scatter, q.scatter);
     upload(c, q.h.rout, q.rout);
-    ensure(c, r->ws, (size_t)q.h.ws_size * 8);
+    int64_t wsz = q.h.ws_size;
+    if (r->use_cholqr) {
+      CholQrPlan cp = build_cholqr(q.h.jobs, q.h.ws_size);
+      wsz = cp.ws_end;
+      const Caps cw = caps({{S_AUX2, wsz}});
+      for (int p = 0; p < 3; ++p) {
+        check_plan(cp.gram[p], cw, "CholQR gram");
+        check_plan(cp.app[p], cw, "CholQR apply");
+        upload(c, cp.gram[p], q.gram[p]);
+        upload(c, cp.app[p], q.app[p]);
+        for (const CholJob& J : cp.cj[p])
+          if (J.g + (int64_t)J.n * J.n > wsz || J.r + (int64_t)J.n * J.n > wsz || J.ri + (int64_t)J.n * J.n > wsz)
+            throw Err{TT_ERR_STATE, "Cholesky job outside the workspace"};
+        q.ncj[p] = (int)cp.cj[p].size();
+        ensure(c, q.cjobs[p], cp.cj[p].size() * sizeof(CholJob) + 16);
+        if (!cp.cj[p].empty())
+          CK(cudaMemcpyAsync(q.cjobs[p].p, cp.cj[p].data(), cp.cj[p].size() * sizeof(CholJob), cudaMemcpyHostToDevice,
+                             st));
+      }
+      check_plan(cp.tt, cw, "CholQR T");
+      check_plan(cp.rf, cw, "CholQR R");
+      upload(c, cp.tt, q.tt);
+      upload(c, cp.rf, q.rf);
+      ensure(c, q.fail, q.h.jobs.size() * sizeof(int) + 16);
+    }
+    ensure(c, r->ws, (size_t)wsz * 8);
     ensure(c, r->Sb, (size_t)q.h.s_size * 8);
     q.valid = true;
     return q;
@@ -395,24 +429,36 @@ struct Eng {
   // ---- GEMM / gather dispatch ---------------------------------------------
   cudaEvent_t prof_begin(int kind, double flops) {
     if (!r->prof) return nullptr;
-    if (r->evused + 2 > r->evpool.size()) {
+    std::vector<cudaEvent_t>& pool = r->capturing ? r->gpool : r->evpool;
+    std::vector<int>& kinds = r->capturing ? r->gkind : r->evkind;
+    size_t& used = r->capturing ? r->gused : r->evused;
+    if (used + 2 > pool.size()) {
       for (int i = 0; i < 256; ++i) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
-        r->evpool.push_back(e);
-        r->evkind.push_back(0);
+        pool.push_back(e);
+        kinds.push_back(0);
       }
     }
-    cudaEvent_t e = r->evpool[r->evused];
-    r->evkind[r->evused] = kind;
-    r->evused += 2;
-    r->kind_flops[kind] += flops;
-    CK(cudaEventRecord(e, st));
+    cudaEvent_t e = pool[used];
+    kinds[used] = kind;
+    used += 2;
+    if (r->capturing) r->graph_kind_flops[kind] += flops;
+    else r->kind_flops[kind] += flops;
+    record(e);
     return e;
   }
   void prof_end(cudaEvent_t e) {
     if (!e) return;
-    CK(cudaEventRecord(r->evpool[r->evused - 1], st));
+    const std::vector<cudaEvent_t>& pool = r->capturing ? r->gpool : r->evpool;
+    const size_t used = r->capturing ? r->gused : r->evused;
+    record(pool[used - 1]);
+  }
+  // inside a stream capture a plain record only orders the graph; the external
+  // flag makes it a record node whose time the replay writes
+  void record(cudaEvent_t e) {
+    if (r->capturing) CK(cudaEventRecordWithFlags(e, st, cudaEventRecordExternal));
+    else CK(cudaEventRecord(e, st));
   }
 
   // tcgen05 eligibility (K-major A and B, 16-byte aligned rows and offsets) and
@@ -739,6 +785,33 @@ struct Eng {
   }
 
   // ---- gauge moves ----------------------------------------------------------
+  // QR of the gathered sector matrices: shifted CholeskyQR3 on all SMs, then
+  // the Householder kernel for the sectors whose Cholesky failed (rank
+  // deficient or too ill-conditioned), or Householder for every sector.
+  void run_qr(QrDev& q, const Bases& b) {
+    cudaEvent_t e = prof_begin(5, 0);
+    run_qr_inner(q, b);
+    prof_end(e);
+  }
+  void run_qr_inner(QrDev& q, const Bases& b) {
+    if (!r->use_cholqr) {
+      CK(launch_qr((const QrJob*)q.jobs.p, (int)q.h.jobs.size(), dptr(r->ws), st));
+      count();
+      return;
+    }
+    CK(cudaMemsetAsync(q.fail.p, 0, q.h.jobs.size() * sizeof(int), st));
+    for (int p = 0; p < 3; ++p) {
+      CK(launch_gemm_f64(q.gram[p].d, b, st));
+      CK(launch_chol_inv((const CholJob*)q.cjobs[p].p, q.ncj[p], dptr(r->ws), (int*)q.fail.p, st));
+      CK(launch_gemm_f64(q.app[p].d, b, st));
+      count(3);
+    }
+    CK(launch_gemm_f64(q.tt.d, b, st));
+    CK(launch_gemm_f64(q.rf.d, b, st));
+    count(2);
+    CK(launch_qr_masked((const QrJob*)q.jobs.p, (int)q.h.jobs.size(), dptr(r->ws), (const int*)q.fail.p, st));
+    count();
+  }
   void qr_left_move(int j) {  // A_j = A_j^L S ; S -> Sb (bond j+1)
     QrDev& q = qr_plan(j, true);
     Bases b{};
@@ -747,10 +820,10 @@ struct Eng {
     b.p[S_AUX] = r->Sb.p;
     b.p[S_AUX2] = r->ws.p;
     CK(launch_copy(q.gather.d, b, st));
-    CK(launch_qr((const QrJob*)q.jobs.p, (int)q.h.jobs.size(), dptr(r->ws), st));
+    run_qr(q, b);
     CK(launch_copy(q.scatter.d, b, st));
     CK(launch_copy(q.rout.d, b, st));
-    count(4);
+    count(3);
   }
   void lq_right_move(int j) {  // A_j = S A_j^R ; S -> Sb (bond j)
     QrDev& q = qr_plan(j, false);
@@ -760,10 +833,10 @@ struct Eng {
     b.p[S_AUX] = r->Sb.p;
     b.p[S_AUX2] = r->ws.p;
     CK(launch_copy(q.gather.d, b, st));
-    CK(launch_qr((const QrJob*)q.jobs.p, (int)q.h.jobs.size(), dptr(r->ws), st));
+    run_qr(q, b);
     CK(launch_copy(q.scatter.d, b, st));
     CK(launch_copy(q.rout.d, b, st));
-    count(4);
+    count(3);
   }
   void absorb_into_left_of(int j) {  // A_j <- S A_j
     DevGemmBuf& g = absorb_left_plan(j);
@@ -1777,6 +1850,10 @@ void alloc_rho_arrays(tt_rho* r) {
   {
     const char* gk = std::getenv("TT_GEMM_KERNEL");
     r->use_tc = !(gk && std::strcmp(gk, "mma") == 0);
+    const char* gg = std::getenv("TT_CUDA_GRAPH");
+    r->use_graph = !(gg && std::strcmp(gg, "0") == 0);
+    const char* gq = std::getenv("TT_QR");
+    r->use_cholqr = !(gq && std::strcmp(gq, "householder") == 0);
   }
   r->sp.assign(N, SiteDev());
   r->bp.assign(N + 1, BondDev());
@@ -1806,7 +1883,11 @@ void free_rho(tt_rho* r) {
   for (auto& e : r->esplit) release(c, e);
   for (auto& s : r->bp) { release(c, s.b1); release(c, s.b2); }
   for (auto* v : {&r->qrl, &r->lqr})
-    for (auto& q : *v) { dfree(c, q.jobs); release(c, q.gather); release(c, q.scatter); release(c, q.rout); }
+    for (auto& q : *v) {
+      dfree(c, q.jobs); release(c, q.gather); release(c, q.scatter); release(c, q.rout);
+      for (int p = 0; p < 3; ++p) { release(c, q.gram[p]); release(c, q.app[p]); dfree(c, q.cjobs[p]); }
+      release(c, q.tt); release(c, q.rf); dfree(c, q.fail);
+    }
   for (auto& g : r->absl) release(c, g);
   for (auto& g : r->absr) release(c, g);
   for (auto& m : r->meas) { release(c, m.t); release(c, m.el); dfree(c, m.items); }
@@ -1934,6 +2015,8 @@ void tt_rho_destroy(tt_rho* rho) {
   if (!rho) return;
   cudaStreamSynchronize(rho->ctx->st);
   for (cudaEvent_t e : rho->evpool) cudaEventDestroy(e);
+  for (cudaEvent_t e : rho->gpool) cudaEventDestroy(e);
+  if (rho->graph) cudaGraphExecDestroy(rho->graph);
   if (rho->ev0) cudaEventDestroy(rho->ev0);
   if (rho->ev1) cudaEventDestroy(rho->ev1);
   free_rho(rho);
@@ -1964,20 +2047,86 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
     e.prepare_all();
     if (!rho->ev0) CK(cudaEventCreate(&rho->ev0));
     if (!rho->ev1) CK(cudaEventCreate(&rho->ev1));
+    cudaStream_t st = rho->ctx->st;
     // statistics accumulate over the calls since the last tt_stats_get
     if (!rho->stats_pending) {
       rho->heff_flops_acc = rho->step_flops_acc = 0;
       rho->launches_acc = 0;
       rho->evused = 0;
-      for (int k = 0; k < 5; ++k) { rho->kind_ms[k] = 0; rho->kind_n[k] = 0; rho->kind_flops[k] = 0; }
-      CK(cudaEventRecord(rho->ev0, rho->ctx->st));
+      for (int k = 0; k < 6; ++k) { rho->kind_ms[k] = 0; rho->kind_n[k] = 0; rho->kind_flops[k] = 0; }
+      CK(cudaEventRecord(rho->ev0, st));
     }
-    for (int s = 0; s < n_steps; ++s) {
+    if (rho->graph && (rho->graph_dtau != dtau || rho->graph_prof != rho->prof)) e.drop_graph();
+    int s = 0;
+    if (!rho->graph && rho->use_graph && n_steps > 0 && st != nullptr && !rho->stats_pending) {
+      // one uncaptured step builds every plan, tensor map and buffer, then one
+      // step is captured (no allocation or host synchronisation happens in it)
       e.sweep_lr(dtau / 4);
       e.sweep_rl(dtau / 4);
       rho->beta += dtau;
+      ++s;
+      const double hf = rho->heff_flops_acc, sf = rho->step_flops_acc;
+      const long long ln = rho->launches_acc;
+      // profiling events of the captured step live in their own pool, created
+      // before the capture
+      rho->gused = 0;
+      for (int k = 0; k < 6; ++k) rho->graph_kind_flops[k] = 0;
+      if (rho->prof)
+        while (rho->gpool.size() < rho->evused + 512) {
+          cudaEvent_t x;
+          CK(cudaEventCreate(&x));
+          rho->gpool.push_back(x);
+          rho->gkind.push_back(0);
+        }
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      rho->capturing = true;
+      bool ok = true;
+      try {
+        e.sweep_lr(dtau / 4);
+        e.sweep_rl(dtau / 4);
+      } catch (...) {
+        ok = false;
+      }
+      rho->capturing = false;
+      cudaError_t ce = cudaStreamEndCapture(st, &g);
+      if (!ok || ce != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        throw Err{TT_ERR_CUDA, "capture of the beta-step failed"};
+      }
+      cudaError_t ie = cudaGraphInstantiate(&rho->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        cudaGetLastError();
+        rho->graph = nullptr;
+        throw Err{TT_ERR_CUDA, "graph instantiation failed"};
+      }
+      rho->graph_dtau = dtau;
+      rho->graph_prof = rho->prof;
+      rho->graph_heff_flops = rho->heff_flops_acc - hf;
+      rho->graph_step_flops = rho->step_flops_acc - sf;
+      rho->graph_launches = rho->launches_acc - ln;
+      // the captured step has not run yet: undo its host-side bookkeeping
+      rho->heff_flops_acc = hf;
+      rho->step_flops_acc = sf;
+      rho->launches_acc = ln;
+      rho->graph_replays = 0;
     }
-    CK(cudaEventRecord(rho->ev1, rho->ctx->st));
+    for (; s < n_steps; ++s) {
+      if (rho->graph) {
+        CK(cudaGraphLaunch(rho->graph, st));
+        rho->heff_flops_acc += rho->graph_heff_flops;
+        rho->step_flops_acc += rho->graph_step_flops;
+        rho->launches_acc += rho->graph_launches;
+        ++rho->graph_replays;
+      } else {
+        e.sweep_lr(dtau / 4);
+        e.sweep_rl(dtau / 4);
+      }
+      rho->beta += dtau;
+    }
+    CK(cudaEventRecord(rho->ev1, st));
     rho->stats.heff_flops = rho->heff_flops_acc;
     rho->stats.step_flops = rho->step_flops_acc;
     rho->stats.launches = rho->launches_acc;
@@ -1999,20 +2148,42 @@ tt_status tt_stats_get(const tt_rho* rho_c, tt_stats* out) {
   tt_rho* rho = const_cast<tt_rho*>(rho_c);
   if (rho->stats_pending) {
     float ms = 0;
-    if (cudaEventSynchronize(rho->ev1) != cudaSuccess || cudaEventElapsedTime(&ms, rho->ev0, rho->ev1) != cudaSuccess) {
+    cudaError_t ce = cudaEventSynchronize(rho->ev1);
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, rho->ev0, rho->ev1);
+    if (ce != cudaSuccess) {
       cudaGetLastError();
+      rho->ctx->err = std::string("step timing events: ") + cudaGetErrorString(ce);
       return TT_ERR_CUDA;
     }
     rho->stats.step_ms = ms;
     for (size_t i = 0; i + 1 < rho->evused; i += 2) {
       float t = 0;
-      if (cudaEventElapsedTime(&t, rho->evpool[i], rho->evpool[i + 1]) != cudaSuccess) {
+      cudaError_t ee = cudaEventElapsedTime(&t, rho->evpool[i], rho->evpool[i + 1]);
+      if (ee != cudaSuccess) {
         cudaGetLastError();
+        rho->ctx->err = std::string("profiling events: ") + cudaGetErrorString(ee);
         return TT_ERR_CUDA;
       }
       rho->kind_ms[rho->evkind[i]] += t;
       rho->kind_n[rho->evkind[i]] += 1;
     }
+    // events inside the graph hold the times of its last replay; every replay
+    // runs the same launches, so they stand for all replays since the reset
+    if (rho->graph_replays > 0 && rho->graph_prof) {
+      for (size_t i = 0; i + 1 < rho->gused; i += 2) {
+        float t = 0;
+        cudaError_t ee = cudaEventElapsedTime(&t, rho->gpool[i], rho->gpool[i + 1]);
+        if (ee != cudaSuccess) {
+          cudaGetLastError();
+          rho->ctx->err = std::string("profiling events inside the graph: ") + cudaGetErrorString(ee);
+          return TT_ERR_CUDA;
+        }
+        rho->kind_ms[rho->gkind[i]] += t * rho->graph_replays;
+        rho->kind_n[rho->gkind[i]] += rho->graph_replays;
+      }
+      for (int k = 0; k < 6; ++k) rho->kind_flops[k] += rho->graph_kind_flops[k] * rho->graph_replays;
+    }
+    rho->graph_replays = 0;
     rho->stats.heff_ms = rho->kind_ms[0];
     rho->stats.heff_launches = rho->kind_n[0];
     rho->stats.env_ms = rho->kind_ms[1];
@@ -2020,6 +2191,7 @@ tt_status tt_stats_get(const tt_rho* rho_c, tt_stats* out) {
     rho->stats.bond_ms = rho->kind_ms[2];
     rho->stats.gather_ms = rho->kind_ms[3];
     rho->stats.gather_launches = rho->kind_n[3];
+    rho->stats.qr_ms = rho->kind_ms[5];
     rho->stats_pending = false;
   }
   *out = rho->stats;

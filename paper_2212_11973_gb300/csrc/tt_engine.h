@@ -102,6 +102,10 @@ struct QrDev {
   QrPlanHost h;
   DBuf jobs;
   DevCopyBuf gather, scatter, rout;
+  // shifted CholeskyQR3 (FP64 GEMMs on all SMs) with Householder fallback
+  DevGemmBuf gram[3], app[3], tt, rf;
+  DBuf cjobs[3], fail;
+  int ncj[3] = {0, 0, 0};
 };
 struct MeasDev {
   bool valid = false;
@@ -130,6 +134,7 @@ struct tt_rho {
   std::vector<tt::DevCopyBuf> esplit;     // per bond: FP64 environment -> padded split copy
   std::vector<char> esplit_ok;
   bool use_tc = true;                     // tcgen05 kernel for eligible split-bf16 GEMMs
+  bool use_cholqr = true;                 // CholeskyQR3 gauge (else Householder only)
   std::vector<tt::SiteDev> sp;
   std::vector<tt::BondDev> bp;
   std::vector<tt::QrDev> qrl, lqr;
@@ -144,12 +149,25 @@ struct tt_rho {
   // per-launch CUDA events (profiling mode): kind 0 = site H_eff GEMMs,
   // 1 = environment GEMMs, 2 = bond H_eff GEMMs, 3 = gather, 4 = other
   bool prof = false;
+  // CUDA graph of one beta-step (the block structure is fixed in 1-TDVP)
+  cudaGraphExec_t graph = nullptr;
+  double graph_dtau = 0.0;
+  bool graph_prof = false;
+  double graph_heff_flops = 0, graph_step_flops = 0;
+  long long graph_launches = 0;
+  bool use_graph = true;
+  bool capturing = false;
+  long long graph_replays = 0;            // since the last tt_stats_get
+  std::vector<cudaEvent_t> gpool;         // profiling events recorded inside the graph
+  std::vector<int> gkind;
+  size_t gused = 0;
+  double graph_kind_flops[6] = {0, 0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> evpool;
   std::vector<int> evkind;
   size_t evused = 0;
-  double kind_ms[5] = {0, 0, 0, 0, 0};
-  long long kind_n[5] = {0, 0, 0, 0, 0};
-  double kind_flops[5] = {0, 0, 0, 0, 0};
+  double kind_ms[6] = {0, 0, 0, 0, 0, 0};
+  long long kind_n[6] = {0, 0, 0, 0, 0, 0};
+  double kind_flops[6] = {0, 0, 0, 0, 0, 0};
   double heff_flops_acc = 0, step_flops_acc = 0;
   long long launches_acc = 0;
 };

@@ -601,7 +601,9 @@ __global__ void nrm_finalize(const double* partial, int nblk, KrylovState* ks, R
 constexpr int QRT = 256;
 constexpr int QR_MAXN = 2048;
 
-__global__ void __launch_bounds__(QRT) qr_kernel(const QrJob* __restrict__ jobs, double* __restrict__ ws) {
+__global__ void __launch_bounds__(QRT) qr_kernel(const QrJob* __restrict__ jobs, double* __restrict__ ws,
+                                                 const int* __restrict__ only) {
+  if (only && !only[blockIdx.x]) return;  // masked launch: fallback sectors only
   const QrJob J = jobs[blockIdx.x];
   const int m = J.m, n = J.n;
   double* A = ws + J.a;
@@ -888,7 +890,99 @@ cudaError_t launch_scale_rc(double* a, long long ld, int rows, int cols, const d
 
 cudaError_t launch_qr(const QrJob* jobs, int njobs, double* ws, cudaStream_t s) {
   if (njobs == 0) return cudaSuccess;
-  qr_kernel<<<njobs, QRT, 0, s>>>(jobs, ws);
+  qr_kernel<<<njobs, QRT, 0, s>>>(jobs, ws, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qr_masked(const QrJob* jobs, int njobs, double* ws, const int* only, cudaStream_t s) {
+  if (njobs == 0) return cudaSuccess;
+  qr_kernel<<<njobs, QRT, 0, s>>>(jobs, ws, only);
+  return cudaGetLastError();
+}
+
+// Cholesky G = R^T R (R upper, G row-major n x n at ws + g) and R^-1, one CTA
+// per job.  Optional diagonal shift s = 11 (m n + n (n + 1)) u tr(G) (shifted
+// CholeskyQR, Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020).  A
+// non-positive or non-finite pivot marks fail[sec] and leaves the job to the
+// Householder fallback.
+__global__ void __launch_bounds__(256) chol_inv_kernel(const CholJob* __restrict__ jobs, double* __restrict__ ws,
+                                                       int* __restrict__ fail) {
+  const CholJob J = jobs[blockIdx.x];
+  const int n = J.n;
+  double* G = ws + J.g;
+  double* R = ws + J.r;
+  double* Ri = ws + J.ri;
+  __shared__ double piv;
+  __shared__ int bad;
+  if (J.shift == 3) {  // more columns than rows: left to the Householder kernel
+    if (threadIdx.x == 0) fail[J.sec] = 1;
+    return;
+  }
+  if (threadIdx.x == 0) {
+    bad = fail[J.sec];
+    if (J.shift == 1 && !bad) {
+      double tr = 0.0;
+      for (int i = 0; i < n; ++i) tr += G[(long long)i * n + i];
+      const double sft = 11.0 * ((double)J.m * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * tr;
+      for (int i = 0; i < n; ++i) G[(long long)i * n + i] += sft;
+    }
+  }
+  __syncthreads();
+  if (bad) return;
+  if (J.shift == 2) {
+    // Third pass: its input should already be orthonormal to working
+    // accuracy; a Gram matrix far from the identity means the first two
+    // passes met a (numerically) rank-deficient block, which the Householder
+    // fallback handles instead.
+    int off = 0;
+    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+      const int i = (int)(e / n), j = (int)(e % n);
+      const double dev = G[e] - (i == j ? 1.0 : 0.0);
+      if (!(fabs(dev) <= 1e-3)) off = 1;
+    }
+    if (__syncthreads_or(off)) {
+      if (threadIdx.x == 0) fail[J.sec] = 1;
+      return;
+    }
+  }
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) R[e] = 0.0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double d = G[(long long)k * n + k];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        fail[J.sec] = 1;
+      }
+      piv = bad ? 1.0 : sqrt(d);
+    }
+    __syncthreads();
+    if (bad) return;
+    const double p = piv;
+    for (int j = k + threadIdx.x; j < n; j += blockDim.x) R[(long long)k * n + j] = G[(long long)k * n + j] / p;
+    __syncthreads();
+    const int w = n - k - 1;  // trailing upper triangle (i, j), k < i <= j
+    for (long long e = threadIdx.x; e < (long long)w * w; e += blockDim.x) {
+      const int i = k + 1 + (int)(e / w), j = k + 1 + (int)(e % w);
+      if (j >= i) G[(long long)i * n + j] -= R[(long long)k * n + i] * R[(long long)k * n + j];
+    }
+    __syncthreads();
+  }
+  // R^-1 (upper), one column per thread: R x = e_j by back substitution
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    for (int i = j + 1; i < n; ++i) Ri[(long long)i * n + j] = 0.0;
+    Ri[(long long)j * n + j] = 1.0 / R[(long long)j * n + j];
+    for (int i = j - 1; i >= 0; --i) {
+      double acc = 0.0;
+      for (int q = i + 1; q <= j; ++q) acc = fma(R[(long long)i * n + q], Ri[(long long)q * n + j], acc);
+      Ri[(long long)i * n + j] = -acc / R[(long long)i * n + i];
+    }
+  }
+}
+
+cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s) {
+  if (njobs == 0) return cudaSuccess;
+  chol_inv_kernel<<<njobs, 256, 0, s>>>(jobs, ws, fail);
   return cudaGetLastError();
 }
 

@@ -96,6 +96,11 @@ cudaError_t k_normalise_inplace(double* v, int64_t n, double* partial, KrylovSta
 
 // Householder QR of a batch of column-major matrices in workspace `ws`.
 cudaError_t launch_qr(const QrJob* jobs, int njobs, double* ws, cudaStream_t s);
+// the same, only for the jobs whose only[job] != 0
+cudaError_t launch_qr_masked(const QrJob* jobs, int njobs, double* ws, const int* only, cudaStream_t s);
+// Cholesky + triangular inverse per job (shifted on request); fail[sec] set on
+// a non-positive pivot.
+cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s);
 // Sign fix diag(R) >= 0 done inside launch_qr.
 
 // Per-block item of the local measurement (d = 4 local space, <= 4 pairs).

@@ -416,4 +416,38 @@ QrPlanHost build_lq_right(const SiteLayout& S, const Bond& BL, bool shrink) {
   return P;
 }
 
+CholQrPlan build_cholqr(const std::vector<QrJob>& jobs, int64_t ws0) {
+  CholQrPlan P;
+  int64_t w = ws0;
+  for (size_t sec = 0; sec < jobs.size(); ++sec) {
+    const QrJob& J = jobs[sec];
+    const int m = J.m, n = J.n;
+    if (m < n || n == 0) {  // rank-deficient by shape: Householder only
+      if (n > 0) P.cj[0].push_back(CholJob{0, 0, 0, m, n, 3, (int)sec});
+      continue;
+    }
+    const int64_t mn = (int64_t)m * n, nn = (int64_t)n * n;
+    const int64_t q0 = w, q1 = q0 + mn, g = q1 + mn, r0 = g + nn, r1 = r0 + nn, r2 = r1 + nn, ri0 = r2 + nn,
+                  ri1 = ri0 + nn, ri2 = ri1 + nn, tt = ri2 + nn;
+    w = tt + nn;
+    const int64_t X[3] = {J.a, q0, q1}, Xo[3] = {q0, q1, J.q}, R[3] = {r0, r1, r2}, RI[3] = {ri0, ri1, ri2};
+    for (int p = 0; p < 3; ++p) {
+      // G = X^T X : A = X^T (row-major n x m, ld m), B = X stored N x K (ld m)
+      P.gram[p].add_group(n, n, mkref(S_AUX2, g), n, 0);
+      P.gram[p].add_seg(mkref(S_AUX2, X[p]), m, 0, mkref(S_AUX2, X[p]), m, 1, m);
+      P.cj[p].push_back(CholJob{g, R[p], RI[p], m, n, p == 0 ? 1 : (p == 2 ? 2 : 0), (int)sec});
+      // Xo^T = RI^T X^T : written row-major (n x m) = Xo column-major
+      P.app[p].add_group(n, m, mkref(S_AUX2, Xo[p]), m, 0);
+      P.app[p].add_seg(mkref(S_AUX2, RI[p]), n, 1, mkref(S_AUX2, X[p]), m, 0, n);
+    }
+    // T^T = R0^T R1^T ; R^T = T^T R2^T (row-major R^T = column-major R)
+    P.tt.add_group(n, n, mkref(S_AUX2, tt), n, 0);
+    P.tt.add_seg(mkref(S_AUX2, r0), n, 1, mkref(S_AUX2, r1), n, 1, n);
+    P.rf.add_group(n, n, mkref(S_AUX2, J.r), n, 0);
+    P.rf.add_seg(mkref(S_AUX2, tt), n, 0, mkref(S_AUX2, r2), n, 1, n);
+  }
+  P.ws_end = w;
+  return P;
+}
+
 }  // namespace tt

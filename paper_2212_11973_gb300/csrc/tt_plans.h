@@ -33,6 +33,17 @@ struct QrPlanHost {
   int64_t ws_size = 0, s_size = 0;
 };
 
+// Shifted CholeskyQR3 for the QR jobs of a gauge move (all in the workspace
+// slot): G = X^T X, Cholesky (+ shift in the first pass), X <- X R^-1, three
+// passes; R = R2 R1 R0 written where the Householder job puts R, Q where it
+// puts Q.  Extra workspace starts at ws0.
+struct CholQrPlan {
+  GemmPlan gram[3], app[3], tt, rf;
+  std::vector<CholJob> cj[3];
+  int64_t ws_end = 0;
+};
+CholQrPlan build_cholqr(const std::vector<QrJob>& jobs, int64_t ws0);
+
 SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& ls, const std::vector<MpoTerm>& terms,
                              const std::vector<Q>& chl, const std::vector<Q>& chr, bool mixed);
 BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed);

@@ -60,7 +60,8 @@ class tt_stats(C.Structure):
                 ("env_flops", C.c_double), ("env_ms", C.c_double), ("bond_ms", C.c_double),
                 ("gather_ms", C.c_double), ("gather_launches", C.c_longlong),
                 ("step_flops", C.c_double), ("step_ms", C.c_double), ("launches", C.c_longlong),
-                ("n_sites", C.c_int), ("max_bond", C.c_int), ("n_sectors_max", C.c_int)]
+                ("n_sites", C.c_int), ("max_bond", C.c_int), ("n_sectors_max", C.c_int),
+                ("qr_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

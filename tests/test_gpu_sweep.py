@@ -110,3 +110,78 @@ def test_ladder_mixed_matches_oracle(tt, ctx, prec, tol):
         r = ref[round(o["beta"], 9)]
         for k in ("energy_per_site", "double_occ"):
             assert _rel(o[k], r[k]) < tol, (o["beta"], k, o[k], r[k])
+
+
+def test_graph_replay_matches_direct_launches(tt):
+    """On a non-default stream a beta-step is captured once as a CUDA graph and
+    replayed; the kernels are deterministic, so the observables must be
+    bitwise equal to the per-launch path (legacy default stream)."""
+    import torch
+    cfg = wl.LADDER_2x4
+    out = []
+    for use_stream in (False, True):
+        stream = torch.cuda.Stream() if use_stream else torch.cuda.default_stream()
+        with torch.cuda.stream(stream):
+            c = tt.Context(stream=stream)
+            mpo = tt.Mpo(c, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
+            rho = tt.Rho(c, mpo, cfg.beta0, tt.run_opts(cfg.D, cfg.krylov, 2))
+            rho.grow(cfg.dtau, 0.2)
+            rho.step(cfg.dtau, 3)
+            out.append(rho.measure())
+            rho.close()
+            mpo.close()
+            c.close()
+    for k in ("lnZ", "energy_per_site", "density", "double_occ"):
+        assert out[0][k] == out[1][k], (k, out[0][k], out[1][k])
+
+
+def _steps_with_qr(tt, monkeypatch, mode, cfg, D, steps, prec):
+    if mode:
+        monkeypatch.setenv("TT_QR", mode)
+    else:
+        monkeypatch.delenv("TT_QR", raising=False)
+    c = tt.Context()
+    mpo = tt.Mpo(c, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
+    rho = tt.Rho(c, mpo, cfg.beta0, tt.run_opts(D, cfg.krylov, prec))
+    rho.grow(cfg.dtau, 0.2)
+    obs = []
+    for _ in range(steps):
+        rho.step(cfg.dtau, 1)
+        obs.append(rho.measure())
+    rho.close()
+    mpo.close()
+    c.close()
+    return obs
+
+
+def test_cholqr_gauge_matches_householder(tt, monkeypatch):
+    """4x8 cylinder at D = 128 (tall sector blocks up to a few hundred rows):
+    the CholeskyQR3 gauge and the Householder-only gauge give the same state
+    up to rounding, so FP64 observables agree to 1e-10."""
+    cfg = wl.CYL_4x8_D256
+    a = _steps_with_qr(tt, monkeypatch, "householder", cfg, 128, 3, 0)
+    b = _steps_with_qr(tt, monkeypatch, None, cfg, 128, 3, 0)
+    for oa, ob in zip(a, b):
+        for k in KEYS_FP64:
+            assert _rel(ob[k], oa[k]) < 1e-10, (oa["beta"], k, ob[k], oa[k])
+
+
+def test_profiled_graph_replay_reports_times(tt):
+    """Profiling events inside the captured beta-step are record nodes: after
+    replays every kernel class reports a positive device time."""
+    import torch
+    cfg = wl.LADDER_2x4
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        c = tt.Context(stream=stream)
+        mpo = tt.Mpo(c, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
+        rho = tt.Rho(c, mpo, cfg.beta0, tt.run_opts(cfg.D, cfg.krylov, 2))
+        rho.grow(cfg.dtau, 0.2)
+        rho.set_profiling(True)
+        rho.step(cfg.dtau, 3)
+        s = rho.stats()
+        rho.close()
+        mpo.close()
+        c.close()
+    assert s["step_ms"] > 0 and s["heff_ms"] > 0 and s["env_ms"] > 0 and s["qr_ms"] > 0
+    assert s["heff_ms"] + s["env_ms"] + s["qr_ms"] < s["step_ms"]
