@@ -148,6 +148,85 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """64 independent 2x8 ladders (drawn U, mu; D cycling 64/96/128), split-BF16
+    x6, all stepped by one tt_batch_step per beta-step.  Replicas for N > 1:
+    every rank runs its own 64 instances."""
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import torch
+    import torch.distributed as dist
+    from paper_2212_11973_gb300 import tantrg as tt
+    from paper_2212_11973_gb300 import workloads as wl
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ws = wl.batch_ladders()
+    w0 = ws[0]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = tt.Context(stream=stream)
+        t_prep = time.perf_counter()
+        b = tt.Batch(ctx, ws, w0.beta0, tt.run_opts(0, w0.krylov, w0.precision))
+        print(f"[batch] created in {time.perf_counter() - t_prep:.1f} s", file=sys.stderr, flush=True)
+        b.grow(w0.dtau, 1.0)
+        print(f"[batch] grown at {time.perf_counter() - t_prep:.1f} s", file=sys.stderr, flush=True)
+        for _ in range(args.warmup):
+            b.step(w0.dtau, 1)
+        torch.cuda.synchronize()
+        print(f"[batch] warm at {time.perf_counter() - t_prep:.1f} s", file=sys.stderr, flush=True)
+        t_prep = time.perf_counter() - t_prep
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(b.n):
+            b.stats(i)  # reset the per-instance accumulators
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                b.step(w0.dtau, 1)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        launches = sum(b.stats(i)["launches"] for i in range(b.n))
+        t_dev = ev0.elapsed_time(ev1) / 1e3
+        if world > 1:
+            tmax = torch.tensor([t_dev], device="cuda")
+            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+            t_dev = float(tmax.item())
+        per_step = t_dev / args.steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        obs = None
+        for _ in range(args.steps):
+            b.step(w0.dtau, 1)
+            obs = b.measure()
+        e2e = (time.perf_counter() - t0) / args.steps
+        b.close()
+        ctx.close()
+    if rank == 0:
+        line = {"metric": "s per beta-step of the 64-ladder batch", "value": per_step / world,
+                "unit": "s/beta-step (batch of 64)", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": per_step * 1e3 / world, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16x6+f64", "data": "synthetic",
+                "config": {"workload": "64 ladders 2x8 (open y), U ~ U[2,10], mu ~ U[-2,0], D in {64,96,128}, "
+                                       "splitmix64 seed 2212119730", "N": 16, "dtau": w0.dtau,
+                           "parallelism": f"replicas x{world}", "prep": f"growth to beta=1 + {args.warmup} steps "
+                                                                         f"({t_prep:.1f} s)",
+                           "l2": "state smaller than L2 (no flush; the batch step is latency-bound)"},
+                "instances_per_s": 64 * world / per_step,
+                "e2e": {"value": e2e / world, "unit": "s/beta-step (batch of 64)", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 64 * 64, "includes": "tt_batch_step + tt_batch_measure"},
+                "gpu_launches": launches, "clocks": clk.summary(), "roofline": None, "cpu_baseline": None,
+                "observables_instance0": {k: obs[0][k] for k in ("beta", "energy_per_site", "density",
+                                                                  "double_occ")}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -156,14 +235,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--D", type=int, default=None, help="override the bond dimension (debug)")
     ap.add_argument("--grow-D", type=int, default=256)
-    ap.add_argument("--workload", default="cl6x12", choices=["cl6x12", "cl4x8", "cl4x8-mixed"])
+    ap.add_argument("--workload", default="cl6x12", choices=["cl6x12", "cl4x8", "cl4x8-mixed", "batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true",
+                    help="skip the mixed-vs-FP64 beta-step from a shared checkpoint")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
 
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.workload == "batch64":
+        run_batch(args)
         return
 
     import torch
@@ -239,6 +323,26 @@ def main():
         e2e = (time.perf_counter() - t0) / (args.steps * world)
         barrier()
 
+        # ---- mixed vs FP64: one beta-step of each from the same checkpoint ----
+        check = None
+        if not args.no_fp64_check and rank == 0:
+            import tempfile
+            with tempfile.TemporaryDirectory() as td:
+                path = os.path.join(td, "rho.ttck")
+                rho.save(path)
+                rho.step(cfg.dtau, 1)
+                om = rho.measure()
+                r64 = tt.Rho.load(ctx, mpo, path, tt.run_opts(D, cfg.krylov, 0))
+                t64 = time.perf_counter()
+                r64.step(cfg.dtau, 1)
+                o64 = r64.measure()
+                t64 = time.perf_counter() - t64
+                r64.close()
+            check = {"beta": om["beta"], "fp64_s_per_step_incl_plans": t64,
+                     "energy_per_site": [om["energy_per_site"], o64["energy_per_site"]],
+                     **{f"rel_err_{k}": abs(om[k] - o64[k]) / abs(o64[k])
+                        for k in ("energy_per_site", "double_occ", "density", "free_energy_per_site")}}
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -277,6 +381,11 @@ def main():
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 56,
                 "includes": "tt_tdvp_step + tt_measure (measurement sweep and observables to host)"},
         "breakdown_ms_per_step": {k: s[k + "_ms"] / args.steps for k in ("heff", "env", "qr", "bond", "gather")},
+        "phases_ms_per_step": {k: s[k + "_ms"] / args.steps
+                               for k in ("site_exp", "bond_exp", "env_update", "absorb", "gauge")},
+        "qr_gauge": {"sectors_per_step": s["qr_sectors"] / args.steps,
+                     "householder_fallbacks_per_step": s["qr_fallbacks"] / args.steps},
+        "mixed_vs_fp64": check,
         "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
         "observables": {k: obs[k] for k in ("beta", "energy_per_site", "density", "double_occ",
                                             "free_energy_per_site")} if obs else None,

@@ -128,6 +128,14 @@ typedef struct {
   double qr_ms;            /* QR gauge factorisations: CholeskyQR3 GEMMs and
                               Cholesky kernels plus the Householder fallback
                               (profiling mode) */
+  double bond_flops;       /* algorithmic flops of the bond H_eff GEMMs */
+  long long qr_sectors;    /* sector matrices factorised by the QR gauge */
+  long long qr_fallbacks;  /* of those, the ones the Householder kernel redid
+                              (Cholesky failed or more columns than rows) */
+  /* whole phases of the sweep (profiling mode; they contain the launches
+     counted above): site exponentials (Lanczos + H_eff applies), bond
+     exponentials, environment updates, absorbs, gauge moves (copies + QR) */
+  double site_exp_ms, bond_exp_ms, env_update_ms, absorb_ms, gauge_ms;
 } tt_stats;
 
 /* ---- context ---------------------------------------------------------- */
@@ -186,6 +194,36 @@ tt_status tt_rho_set_profiling(tt_rho* rho, int on);
 
 /* Current bond dimensions: writes N+1 ints (host) to dims. */
 tt_status tt_rho_bond_dims(const tt_rho* rho, int* dims, int n);
+/* U(1)xU(1) sectors of bond k (0..N): *nsec = their number; if cap >= *nsec
+ * the charges (particle number n and s = n_up - n_dn, ket minus bra of the
+ * Choi pair summed over the sites left of the bond) and dimensions are
+ * written to the host arrays qn, qs, dims in the engine's sector order, else
+ * TT_ERR_INVALID_ARG with only *nsec set. */
+tt_status tt_rho_bond_sectors(const tt_rho* rho, int k, int* qn, int* qs, int* dims, int cap, int* nsec);
+
+/* ---- batch of independent instances (many small models evolved together,
+ *      e.g. 64 ladders 2x8 with drawn U, mu and D) ----------------------------
+ *
+ * Instance i is the model models[i] at bond dimension D_max[i], initialised
+ * like tt_rho_create (taylor order 1, beta0) with the other fields of opts.
+ * Every instance owns a context, a CUDA stream and its captured beta-step
+ * graph; tt_batch_step waits for the work already queued on ctx's stream,
+ * replays all instances concurrently, and makes ctx's stream wait for all of
+ * them (asynchronous, like tt_tdvp_step).  tt_batch_grow runs the growth stage
+ * of every instance (synchronous).  tt_batch_measure writes n tt_obs (host,
+ * caller-owned; synchronises).  On error the message names the instance; the
+ * batch is then only safe to destroy.  The library owns the batch; free it with
+ * tt_batch_destroy. */
+tt_status tt_batch_create(tt_ctx* ctx, int n, const tt_model* models, const int* D_max, double beta0,
+                          const tt_run_opts* opts, tt_batch** out);
+void tt_batch_destroy(tt_batch* b);
+int tt_batch_size(const tt_batch* b);
+tt_status tt_batch_grow(tt_batch* b, double dtau, double beta_max);
+tt_status tt_batch_step(tt_batch* b, double dtau, int n_steps);
+tt_status tt_batch_measure(tt_batch* b, tt_obs* out_n);
+/* tt_stats_get of instance i; profiling switched for every instance. */
+tt_status tt_batch_stats(tt_batch* b, int i, tt_stats* out);
+tt_status tt_batch_set_profiling(tt_batch* b, int on);
 
 /* ---- checkpoint (versioned little-endian binary: sector tables, FP64
  *      blocks, beta, logscale) ---------------------------------------------- */

@@ -201,13 +201,14 @@ struct QrJob {
   int64_t a, q, r;
   int m, n;
 };
-// One Cholesky + inverse: G (n x n row-major) -> R (upper, row-major), R^-1.
-// shift: 1 adds the CholeskyQR shift to G first; 2 first checks that G is the
-// identity to 1e-3 (the input of the last pass); 3 only flags the sector (m < n);
-// `sec` indexes the failure flag.
+// One Cholesky + inverse: G = sum of `parts` partial Gram matrices at g + s n^2
+// (upper triangles, n x n row-major) -> R (upper, row-major), R^-1.  shift: 1
+// adds the CholeskyQR shift to G first; 2 marks the last pass, whose input is
+// orthonormal to working accuracy (G = I + E, |E| small); 3 only flags the
+// sector (m < n).  `sec` indexes the failure flag.
 struct CholJob {
   int64_t g, r, ri;
-  int m, n, shift, sec;
+  int m, n, shift, sec, parts;
 };
 
 }  // namespace tt

@@ -63,6 +63,7 @@ void dfree(tt_ctx* c, DBuf& b) {
 
 void ensure(tt_ctx* c, DBuf& b, size_t bytes) {
   if (bytes <= b.bytes && b.p) return;
+  if (b.p) ++c->buf_gen;
   dfree(c, b);
   size_t want = std::max<size_t>(bytes, 256);
   b.p = dalloc(c, want);
@@ -133,6 +134,9 @@ void upload(tt_ctx* c, const CopyPlan& p, DevCopyBuf& o) {
   CK(cudaStreamSynchronize(c->st));
   o.d.items = (CItem*)o.buf.p;
   o.d.nitems = (int)p.items.size();
+  o.d.maxtiles = 0;
+  for (const CItem& it : p.items)
+    o.d.maxtiles = std::max<int64_t>(o.d.maxtiles, (int64_t)((it.rows + 31) / 32) * ((it.cols + 31) / 32));
   o.host = p;
   o.checked = false;
 }
@@ -237,6 +241,8 @@ struct Eng {
   void invalidate_bond(int k) {
     drop_graph();
     // plans touching bond k
+    if (k - 1 >= 0) r->sp64[k - 1].valid = false;
+    if (k < r->N) r->sp64[k].valid = false;
     if (k - 1 >= 0) { r->sp[k - 1].valid = false; r->qrl[k - 1].valid = false; r->lqr[k - 1].valid = false; r->meas[k - 1].valid = false; }
     if (k < r->N) { r->sp[k].valid = false; r->qrl[k].valid = false; r->lqr[k].valid = false; r->meas[k].valid = false; }
     r->bp[k].valid = false;
@@ -280,6 +286,22 @@ struct Eng {
   void ensure_site_buf(int j) { ensure(c, r->A[j], (size_t)r->lay[j].size * sizeof(double)); }
 
   // ---- plans --------------------------------------------------------------
+  // FP64 plans of site j whatever the precision (the measurement's energy)
+  SiteDev& site_plan_fp64(int j) {
+    if (!mixed()) return site_plan(j);
+    SiteDev& s = r->sp64[j];
+    if (s.valid) return s;
+    const Mpo& m = M();
+    s.h = build_site_plan(r->bond[j], r->bond[j + 1], m.ls, m.site[j].terms, m.chan[j], m.chan[j + 1], false);
+    validate_site(s.h, r->bond[j], r->bond[j + 1], m.chan[j], m.chan[j + 1], false);
+    upload(c, s.h.s1, s.s1);
+    upload(c, s.h.s2, s.s2);
+    upload(c, s.h.s3, s.s3);
+    ensure(c, r->T1, (size_t)std::max(s.h.t1_size, s.h.u1_size) * 8);
+    ensure(c, r->T2, (size_t)std::max(s.h.t2_size, s.h.u2_size) * 8);
+    s.valid = true;
+    return s;
+  }
   SiteDev& site_plan(int j) {
     SiteDev& s = r->sp[j];
     if (s.valid) return s;
@@ -324,11 +346,22 @@ struct Eng {
     b.h = build_bond_plan(r->bond[k], M().chan[k], mixed());
     {
       int64_t e = make_env_layout(r->bond[k], M().chan[k], mixed()).size;
-      check_plan(b.h.b1, caps({{S_X, b.h.mat.size}, {S_L, e}, {S_T1, b.h.t_size}}), "B1");
-      check_plan(b.h.b2, caps({{S_T2, b.h.t_size}, {S_R, e}, {S_Y, b.h.mat.size}}), "B2");
+      const int64_t xcap = mixed() ? b.h.xt_size : b.h.mat.size, tcap = mixed() ? b.h.tp_size : b.h.t_size;
+      check_plan(b.h.b1, caps({{S_X, xcap}, {S_L, e}, {S_T1, b.h.t_size}}), "B1");
+      check_plan(b.h.b2, caps({{S_T2, tcap}, {S_R, e}, {S_Y, b.h.mat.size}}), "B2");
+      if (mixed()) {
+        check_plan(b.h.xsplit, caps({{S_X, b.h.mat.size}, {S_Y, b.h.xt_size}}), "B x split");
+        check_plan(b.h.tsplit, caps({{S_T1, b.h.t_size}, {S_Y, b.h.tp_size}}), "B T split");
+      }
     }
     upload(c, b.h.b1, b.b1);
     upload(c, b.h.b2, b.b2);
+    if (mixed()) {
+      upload(c, b.h.xsplit, b.xs);
+      upload(c, b.h.tsplit, b.ts);
+      ensure(c, r->Xs, (size_t)std::max<int64_t>(b.h.xt_size, 1) * 2 * r->nsplit);
+      ensure(c, r->T2, (size_t)std::max<int64_t>(b.h.tp_size, 1) * 2 * r->nsplit);
+    }
     ensure(c, r->T1, (size_t)b.h.t_size * 8);
     ensure(c, r->T2, (size_t)b.h.t_size * 8);
     b.valid = true;
@@ -381,7 +414,7 @@ struct Eng {
         upload(c, cp.gram[p], q.gram[p]);
         upload(c, cp.app[p], q.app[p]);
         for (const CholJob& J : cp.cj[p])
-          if (J.g + (int64_t)J.n * J.n > wsz || J.r + (int64_t)J.n * J.n > wsz || J.ri + (int64_t)J.n * J.n > wsz)
+          if (J.g + (int64_t)J.parts * J.n * J.n > wsz || J.parts < 1 || J.r + (int64_t)J.n * J.n > wsz || J.ri + (int64_t)J.n * J.n > wsz)
             throw Err{TT_ERR_STATE, "Cholesky job outside the workspace"};
         q.ncj[p] = (int)cp.cj[p].size();
         ensure(c, q.cjobs[p], cp.cj[p].size() * sizeof(CholJob) + 16);
@@ -427,8 +460,10 @@ struct Eng {
   }
 
   // ---- GEMM / gather dispatch ---------------------------------------------
-  cudaEvent_t prof_begin(int kind, double flops) {
-    if (!r->prof) return nullptr;
+  // Event pair around a launch or a whole phase; pairs may nest.  Returns the
+  // pair's index (or -1 when profiling is off).
+  long prof_begin(int kind, double flops) {
+    if (!r->prof) return -1;
     std::vector<cudaEvent_t>& pool = r->capturing ? r->gpool : r->evpool;
     std::vector<int>& kinds = r->capturing ? r->gkind : r->evkind;
     size_t& used = r->capturing ? r->gused : r->evused;
@@ -440,19 +475,18 @@ struct Eng {
         kinds.push_back(0);
       }
     }
-    cudaEvent_t e = pool[used];
+    const long idx = (long)used;
     kinds[used] = kind;
     used += 2;
     if (r->capturing) r->graph_kind_flops[kind] += flops;
     else r->kind_flops[kind] += flops;
-    record(e);
-    return e;
+    record(pool[idx]);
+    return idx;
   }
-  void prof_end(cudaEvent_t e) {
-    if (!e) return;
+  void prof_end(long idx) {
+    if (idx < 0) return;
     const std::vector<cudaEvent_t>& pool = r->capturing ? r->gpool : r->evpool;
-    const size_t used = r->capturing ? r->gused : r->evused;
-    record(pool[used - 1]);
+    record(pool[idx + 1]);
   }
   // inside a stream capture a plain record only orders the graph; the external
   // flag makes it a record node whose time the replay writes
@@ -484,20 +518,28 @@ struct Eng {
       g.ntiles128 = (int)tiles.size();
     }
     if (!g.tc_ok) return false;
+    // the maps depend only on the slots the A and B operands live in
+    unsigned used = 0;
+    for (const GSeg& sg : g.host.segs) used |= (1u << (int)(sg.A >> 56)) | (1u << (int)(sg.B >> 56));
     bool same = true;
-    for (int i = 0; i < 8; ++i) same = same && g.key_p[i] == b.p[i] && g.key_lo[i] == b.lo[i];
+    for (int i = 0; i < 8; ++i)
+      if (used & (1u << i)) same = same && g.key_p[i] == b.p[i] && g.key_lo[i] == b.lo[i];
     if (same && g.maps.p) return true;
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
+    // a captured step must replay the uploads of the uncaptured one
+    if (r->capturing) throw Err{TT_ERR_STATE, "tensor-map operands moved during graph capture"};
+    // looked up once per process (thread-safe static initialisation)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
       cudaDriverEntryPointQueryResult q;
       void* fn = nullptr;
-      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-          !fn) {
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess) {
         cudaGetLastError();
-        g.tc_ok = false;
-        return false;
+        fn = nullptr;
       }
-      encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+      return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }();
+    if (!encode) {
+      g.tc_ok = false;
+      return false;
     }
     const size_t nseg = g.host.segs.size();
     std::vector<CUtensorMap> maps(2 * nseg);
@@ -538,8 +580,8 @@ struct Eng {
   }
 
   void gemm(DevGemmBuf& g, const Bases& b, bool use_mixed, int kind = 4) {
-    cudaEvent_t e = prof_begin(kind, g.d.flops);
-    if (use_mixed && r->use_tc && kind == 0 && prep_tc(g, b)) {
+    const long e = prof_begin(kind, g.d.flops);
+    if (use_mixed && r->use_tc && prep_tc(g, b)) {
       if (!r->tcerr.p) {
         ensure(c, r->tcerr, 16);
         CK(cudaMemsetAsync(r->tcerr.p, 0, 16, st));
@@ -555,7 +597,7 @@ struct Eng {
     count();
   }
   void gather(const DevGatherBuf& g, const Bases& b, int in, int out) {
-    cudaEvent_t e = prof_begin(3, 0);
+    const long e = prof_begin(3, 0);
     CK(launch_gather(g.d, b, in, out, st));
     prof_end(e);
     count();
@@ -624,7 +666,7 @@ struct Eng {
   // ---- applies ------------------------------------------------------------
   // y = H^(1)_j x   (x, y device FP64 in the site-j layout)
   void apply_site(int j, const double* x, double* y, bool force_fp64 = false) {
-    SiteDev& s = site_plan(j);
+    SiteDev& s = force_fp64 ? site_plan_fp64(j) : site_plan(j);
     need_site(j, s, true, true);
     Bases b{};
     b.p[S_Y] = y;
@@ -662,22 +704,32 @@ struct Eng {
       need(r->R[k], e * 8, "R");
       if (mixed()) { need(r->Lsp[k], r->Lpsize[k] * el, "Lsp"); need(r->Rsp[k], r->Rpsize[k] * el, "Rsp"); }
       need(r->T1, bd.h.t_size * 8, "T1");
-      need(r->T2, bd.h.t_size * el, "T2");
-      need(r->W, bd.h.mat.size * 8, "W");
-      need(r->Xn, bd.h.mat.size * 2 * std::max(r->nsplit, 1), "Xn");
+      need(r->T2, (mixed() ? bd.h.tp_size : bd.h.t_size) * el, "T2");
+      if (mixed()) need(r->Xs, std::max<int64_t>(bd.h.xt_size, 1) * 2 * r->nsplit, "Xs");
     }
     Bases b{};
     b.p[S_Y] = y;
     b.p[S_T1] = r->T1.p;
     if (mixed()) {
-      int64_t n = bd.h.mat.size;
-      split(x, n, r->Xn.p);
-      b.p[S_X] = r->Xn.p; b.lo[S_X] = n;
+      {  // x -> transposed padded split (B operand of B1)
+        Bases bx{};
+        bx.p[S_X] = (void*)x;
+        bx.p[S_Y] = r->Xs.p; bx.lo[S_Y] = bd.h.xt_size;
+        CK(launch_split_copy(bd.xs.d, bx, r->nsplit, st));
+        count();
+      }
+      b.p[S_X] = r->Xs.p; b.lo[S_X] = bd.h.xt_size;
       b.p[S_L] = r->Lsp[k].p; b.lo[S_L] = r->Lpsize[k];
       b.p[S_R] = r->Rsp[k].p; b.lo[S_R] = r->Rpsize[k];
       gemm(bd.b1, b, true, 2);  // T1 in FP64
-      split((const double*)r->T1.p, bd.h.t_size, r->T2.p);
-      b.p[S_T2] = r->T2.p; b.lo[S_T2] = bd.h.t_size;
+      {  // T1 -> padded split (A operand of B2)
+        Bases bt{};
+        bt.p[S_T1] = r->T1.p;
+        bt.p[S_Y] = r->T2.p; bt.lo[S_Y] = bd.h.tp_size;
+        CK(launch_split_copy(bd.ts.d, bt, r->nsplit, st));
+        count();
+      }
+      b.p[S_T2] = r->T2.p; b.lo[S_T2] = bd.h.tp_size;
       gemm(bd.b2, b, true, 2);
     } else {
       b.p[S_X] = (void*)x;
@@ -777,11 +829,15 @@ struct Eng {
 
   void site_exp(int j, double t) {
     double* x = dptr(r->A[j]);
+    const long e = prof_begin(6, 0);
     lanczos(x, r->lay[j].size, t, [&](const double* q, double* y) { apply_site(j, q, y); });
+    prof_end(e);
   }
   void bond_exp(int k, double t) {
     double* S = dptr(r->Sb);
+    const long e = prof_begin(7, 0);
     lanczos(S, make_bondmat_layout(r->bond[k]).size, t, [&](const double* q, double* y) { apply_bond(k, q, y); });
+    prof_end(e);
   }
 
   // ---- gauge moves ----------------------------------------------------------
@@ -789,7 +845,7 @@ struct Eng {
   // the Householder kernel for the sectors whose Cholesky failed (rank
   // deficient or too ill-conditioned), or Householder for every sector.
   void run_qr(QrDev& q, const Bases& b) {
-    cudaEvent_t e = prof_begin(5, 0);
+    const long e = prof_begin(5, 0);
     run_qr_inner(q, b);
     prof_end(e);
   }
@@ -809,7 +865,13 @@ struct Eng {
     CK(launch_gemm_f64(q.tt.d, b, st));
     CK(launch_gemm_f64(q.rf.d, b, st));
     count(2);
-    CK(launch_qr_masked((const QrJob*)q.jobs.p, (int)q.h.jobs.size(), dptr(r->ws), (const int*)q.fail.p, st));
+    if (!r->qrfb.p) {
+      ensure(c, r->qrfb, 16);
+      CK(cudaMemsetAsync(r->qrfb.p, 0, 16, st));
+    }
+    r->qr_sectors_acc += (long long)q.h.jobs.size();
+    CK(launch_qr_masked((const QrJob*)q.jobs.p, (int)q.h.jobs.size(), dptr(r->ws), (const int*)q.fail.p,
+                        (int*)r->qrfb.p, st));
     count();
   }
   void qr_left_move(int j) {  // A_j = A_j^L S ; S -> Sb (bond j+1)
@@ -860,25 +922,33 @@ struct Eng {
   }
 
   // ---- 1-TDVP ---------------------------------------------------------------
+  // phase timing (profiling mode): 6 site exponentials, 7 bond
+  // exponentials, 8 environment updates, 9 absorbs, 10 gauge moves
+  template <class F>
+  void phase(int kind, F&& f) {
+    const long e = prof_begin(kind, 0);
+    f();
+    prof_end(e);
+  }
   void sweep_lr(double tau) {
     const int N = r->N;
     for (int j = 0; j < N; ++j) {
       site_exp(j, -tau);
       if (j == N - 1) break;
-      qr_left_move(j);
-      update_left_env(j);
+      phase(10, [&] { qr_left_move(j); });
+      phase(8, [&] { update_left_env(j); });
       bond_exp(j + 1, +tau);
-      absorb_into_left_of(j + 1);
+      phase(9, [&] { absorb_into_left_of(j + 1); });
     }
   }
   void sweep_rl(double tau) {
     for (int j = r->N - 1; j >= 0; --j) {
       site_exp(j, -tau);
       if (j == 0) break;
-      lq_right_move(j);
-      update_right_env(j);
+      phase(10, [&] { lq_right_move(j); });
+      phase(8, [&] { update_right_env(j); });
       bond_exp(j, +tau);
-      absorb_into_right_of(j - 1);
+      phase(9, [&] { absorb_into_right_of(j - 1); });
     }
   }
 
@@ -1856,6 +1926,7 @@ void alloc_rho_arrays(tt_rho* r) {
     r->use_cholqr = !(gq && std::strcmp(gq, "householder") == 0);
   }
   r->sp.assign(N, SiteDev());
+  r->sp64.assign(N, SiteDev());
   r->bp.assign(N + 1, BondDev());
   r->qrl.assign(N, QrDev());
   r->lqr.assign(N, QrDev());
@@ -1876,12 +1947,13 @@ void free_rho(tt_rho* r) {
   for (auto& b : r->A) dfree(c, b);
   for (auto* v : {&r->L, &r->R, &r->Lsp, &r->Rsp})
     for (auto& b : *v) dfree(c, b);
-  for (auto& s : r->sp) {
-    release(c, s.s1); release(c, s.s2); release(c, s.s3); release(c, s.s3l); release(c, s.r1); release(c, s.r2);
-    release(c, s.r3); release(c, s.xs);
-  }
+  for (auto* v : {&r->sp, &r->sp64})
+    for (auto& s : *v) {
+      release(c, s.s1); release(c, s.s2); release(c, s.s3); release(c, s.s3l); release(c, s.r1); release(c, s.r2);
+      release(c, s.r3); release(c, s.xs);
+    }
   for (auto& e : r->esplit) release(c, e);
-  for (auto& s : r->bp) { release(c, s.b1); release(c, s.b2); }
+  for (auto& s : r->bp) { release(c, s.b1); release(c, s.b2); release(c, s.xs); release(c, s.ts); }
   for (auto* v : {&r->qrl, &r->lqr})
     for (auto& q : *v) {
       dfree(c, q.jobs); release(c, q.gather); release(c, q.scatter); release(c, q.rout);
@@ -1891,7 +1963,7 @@ void free_rho(tt_rho* r) {
   for (auto& g : r->absl) release(c, g);
   for (auto& g : r->absr) release(c, g);
   for (auto& m : r->meas) { release(c, m.t); release(c, m.el); dfree(c, m.items); }
-  for (DBuf* b : {&r->Qk, &r->W, &r->Xs, &r->Xn, &r->T1, &r->T2, &r->Sb, &r->ws, &r->partial, &r->ks, &r->rs, &r->tmp, &r->obs, &r->el0, &r->el1, &r->tcerr})
+  for (DBuf* b : {&r->Qk, &r->W, &r->Xs, &r->Xn, &r->T1, &r->T2, &r->Sb, &r->ws, &r->partial, &r->ks, &r->rs, &r->tmp, &r->obs, &r->el0, &r->el1, &r->tcerr, &r->qrfb})
     dfree(c, *b);
 }
 
@@ -2052,11 +2124,14 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
     if (!rho->stats_pending) {
       rho->heff_flops_acc = rho->step_flops_acc = 0;
       rho->launches_acc = 0;
+      rho->qr_sectors_acc = 0;
       rho->evused = 0;
-      for (int k = 0; k < 6; ++k) { rho->kind_ms[k] = 0; rho->kind_n[k] = 0; rho->kind_flops[k] = 0; }
+      for (int k = 0; k < 11; ++k) { rho->kind_ms[k] = 0; rho->kind_n[k] = 0; rho->kind_flops[k] = 0; }
       CK(cudaEventRecord(rho->ev0, st));
     }
-    if (rho->graph && (rho->graph_dtau != dtau || rho->graph_prof != rho->prof)) e.drop_graph();
+    if (rho->graph && (rho->graph_dtau != dtau || rho->graph_prof != rho->prof ||
+                       rho->graph_buf_gen != rho->ctx->buf_gen))
+      e.drop_graph();
     int s = 0;
     if (!rho->graph && rho->use_graph && n_steps > 0 && st != nullptr && !rho->stats_pending) {
       // one uncaptured step builds every plan, tensor map and buffer, then one
@@ -2066,11 +2141,11 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
       rho->beta += dtau;
       ++s;
       const double hf = rho->heff_flops_acc, sf = rho->step_flops_acc;
-      const long long ln = rho->launches_acc;
+      const long long ln = rho->launches_acc, qn = rho->qr_sectors_acc;
       // profiling events of the captured step live in their own pool, created
       // before the capture
       rho->gused = 0;
-      for (int k = 0; k < 6; ++k) rho->graph_kind_flops[k] = 0;
+      for (int k = 0; k < 11; ++k) rho->graph_kind_flops[k] = 0;
       if (rho->prof)
         while (rho->gpool.size() < rho->evused + 512) {
           cudaEvent_t x;
@@ -2079,6 +2154,7 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
           rho->gkind.push_back(0);
         }
       cudaGraph_t g = nullptr;
+      const unsigned long long gen0 = rho->ctx->buf_gen;
       CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       rho->capturing = true;
       bool ok = true;
@@ -2090,6 +2166,7 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
       }
       rho->capturing = false;
       cudaError_t ce = cudaStreamEndCapture(st, &g);
+      if (rho->ctx->buf_gen != gen0) ok = false;  // a buffer was replaced inside the capture
       if (!ok || ce != cudaSuccess || !g) {
         cudaGetLastError();
         if (g) cudaGraphDestroy(g);
@@ -2104,9 +2181,12 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
       }
       rho->graph_dtau = dtau;
       rho->graph_prof = rho->prof;
+      rho->graph_buf_gen = rho->ctx->buf_gen;
       rho->graph_heff_flops = rho->heff_flops_acc - hf;
       rho->graph_step_flops = rho->step_flops_acc - sf;
       rho->graph_launches = rho->launches_acc - ln;
+      rho->graph_qr_sectors = rho->qr_sectors_acc - qn;
+      rho->qr_sectors_acc = qn;
       // the captured step has not run yet: undo its host-side bookkeeping
       rho->heff_flops_acc = hf;
       rho->step_flops_acc = sf;
@@ -2119,6 +2199,7 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
         rho->heff_flops_acc += rho->graph_heff_flops;
         rho->step_flops_acc += rho->graph_step_flops;
         rho->launches_acc += rho->graph_launches;
+        rho->qr_sectors_acc += rho->graph_qr_sectors;
         ++rho->graph_replays;
       } else {
         e.sweep_lr(dtau / 4);
@@ -2130,6 +2211,7 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
     rho->stats.heff_flops = rho->heff_flops_acc;
     rho->stats.step_flops = rho->step_flops_acc;
     rho->stats.launches = rho->launches_acc;
+    rho->stats.qr_sectors = rho->qr_sectors_acc;
     rho->stats.n_sites = rho->N;
     rho->stats_pending = true;
   });
@@ -2181,7 +2263,7 @@ tt_status tt_stats_get(const tt_rho* rho_c, tt_stats* out) {
         rho->kind_ms[rho->gkind[i]] += t * rho->graph_replays;
         rho->kind_n[rho->gkind[i]] += rho->graph_replays;
       }
-      for (int k = 0; k < 6; ++k) rho->kind_flops[k] += rho->graph_kind_flops[k] * rho->graph_replays;
+      for (int k = 0; k < 11; ++k) rho->kind_flops[k] += rho->graph_kind_flops[k] * rho->graph_replays;
     }
     rho->graph_replays = 0;
     rho->stats.heff_ms = rho->kind_ms[0];
@@ -2189,9 +2271,29 @@ tt_status tt_stats_get(const tt_rho* rho_c, tt_stats* out) {
     rho->stats.env_ms = rho->kind_ms[1];
     rho->stats.env_flops = rho->kind_flops[1];
     rho->stats.bond_ms = rho->kind_ms[2];
+    rho->stats.bond_flops = rho->kind_flops[2];
     rho->stats.gather_ms = rho->kind_ms[3];
     rho->stats.gather_launches = rho->kind_n[3];
     rho->stats.qr_ms = rho->kind_ms[5];
+    rho->stats.site_exp_ms = rho->kind_ms[6];
+    rho->stats.bond_exp_ms = rho->kind_ms[7];
+    rho->stats.env_update_ms = rho->kind_ms[8];
+    rho->stats.absorb_ms = rho->kind_ms[9];
+    rho->stats.gauge_ms = rho->kind_ms[10];
+    rho->stats.qr_fallbacks = 0;
+    if (rho->qrfb.p) {
+      int nfb = 0;
+      cudaStream_t cs = rho->ctx->st;
+      cudaError_t fe = cudaMemcpyAsync(&nfb, rho->qrfb.p, sizeof(int), cudaMemcpyDeviceToHost, cs);
+      if (fe == cudaSuccess) fe = cudaMemsetAsync(rho->qrfb.p, 0, sizeof(int), cs);
+      if (fe == cudaSuccess) fe = cudaStreamSynchronize(cs);
+      if (fe != cudaSuccess) {
+        cudaGetLastError();
+        rho->ctx->err = std::string("QR fallback counter: ") + cudaGetErrorString(fe);
+        return TT_ERR_CUDA;
+      }
+      rho->stats.qr_fallbacks = nfb;
+    }
     rho->stats_pending = false;
   }
   *out = rho->stats;
@@ -2205,6 +2307,19 @@ tt_status tt_stats_get(const tt_rho* rho_c, tt_stats* out) {
 tt_status tt_rho_bond_dims(const tt_rho* rho, int* dims, int n) {
   if (!rho || !dims || n < rho->N + 1) return TT_ERR_INVALID_ARG;
   for (int k = 0; k <= rho->N; ++k) dims[k] = (int)rho->bond[k].total();
+  return TT_OK;
+}
+
+tt_status tt_rho_bond_sectors(const tt_rho* rho, int k, int* qn, int* qs, int* dims, int cap, int* nsec) {
+  if (!rho || !nsec || k < 0 || k > rho->N) return TT_ERR_INVALID_ARG;
+  const tt::Bond& B = rho->bond[k];
+  *nsec = B.nsec();
+  if (cap < B.nsec() || !qn || !qs || !dims) return TT_ERR_INVALID_ARG;
+  for (int i = 0; i < B.nsec(); ++i) {
+    qn[i] = B.q[i].n;
+    qs[i] = B.q[i].s;
+    dims[i] = B.dim[i];
+  }
   return TT_OK;
 }
 

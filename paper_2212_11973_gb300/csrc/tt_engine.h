@@ -13,6 +13,9 @@
 
 struct tt_ctx {
   cudaStream_t st = nullptr;
+  // bumped whenever a device buffer is replaced by a larger one: a captured
+  // graph holds raw pointers and is only replayed while this is unchanged
+  unsigned long long buf_gen = 0;
   tt_alloc_cb cb{};
   bool has_cb = false;
   std::string err;
@@ -96,6 +99,7 @@ struct BondDev {
   bool valid = false;
   BondPlanHost h;
   DevGemmBuf b1, b2;
+  DevCopyBuf xs, ts;  // mixed precision: padded split copies of x and T
 };
 struct QrDev {
   bool valid = false;
@@ -136,12 +140,14 @@ struct tt_rho {
   bool use_tc = true;                     // tcgen05 kernel for eligible split-bf16 GEMMs
   bool use_cholqr = true;                 // CholeskyQR3 gauge (else Householder only)
   std::vector<tt::SiteDev> sp;
+  std::vector<tt::SiteDev> sp64;
+  unsigned long long graph_buf_gen = 0;  // FP64 site plans used by the measurement in mixed mode
   std::vector<tt::BondDev> bp;
   std::vector<tt::QrDev> qrl, lqr;
   std::vector<tt::DevGemmBuf> absl, absr;
   std::vector<char> absl_ok, absr_ok;
   std::vector<tt::MeasDev> meas;
-  tt::DBuf Qk, W, Xs, Xn, T1, T2, Sb, ws, partial, ks, rs, tmp, obs, el0, el1, tcerr;
+  tt::DBuf Qk, W, Xs, Xn, T1, T2, Sb, ws, partial, ks, rs, tmp, obs, el0, el1, tcerr, qrfb;
   int64_t ldq = 0;
   tt_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -161,13 +167,14 @@ struct tt_rho {
   std::vector<cudaEvent_t> gpool;         // profiling events recorded inside the graph
   std::vector<int> gkind;
   size_t gused = 0;
-  double graph_kind_flops[6] = {0, 0, 0, 0, 0, 0};
+  double graph_kind_flops[11] = {0};
   std::vector<cudaEvent_t> evpool;
   std::vector<int> evkind;
   size_t evused = 0;
-  double kind_ms[6] = {0, 0, 0, 0, 0, 0};
-  long long kind_n[6] = {0, 0, 0, 0, 0, 0};
-  double kind_flops[6] = {0, 0, 0, 0, 0, 0};
+  double kind_ms[11] = {0};
+  long long kind_n[11] = {0};
+  double kind_flops[11] = {0};
   double heff_flops_acc = 0, step_flops_acc = 0;
   long long launches_acc = 0;
+  long long qr_sectors_acc = 0, graph_qr_sectors = 0;
 };

@@ -252,88 +252,118 @@ __global__ void __launch_bounds__(128) gemm_bf16_split_kernel(const GGroup* __re
 }
 
 // ---------------------------------------------------------------------------
-// W gather: dst[r, c] = sum_k coef_k src_k[r, c]  (one CTA per item).
+// W gather: dst[r, c] = sum_k coef_k src_k[r, c]  (one CTA per item, rows
+// strided over the 8 warps, columns over the lanes).  FP64 in, FP64 out for
+// the FP64 path.  Mixed path: the sources are the FP32 outputs of S1, so the
+// sum and the split into bf16 levels run in FP32 (GB300 has about 1/64 of
+// its FP32 rate in FP64); each level's remainder is exact in FP32.
 // ---------------------------------------------------------------------------
+template <int NS>
+__device__ __forceinline__ void store_split_f32(__nv_bfloat16* p, long long lo, float v) {
+#pragma unroll
+  for (int l = 0; l < NS; ++l) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    p[l * lo] = h;
+    v -= __bfloat162float(h);
+  }
+}
+// FP64 value: the first level is rounded from the double and its remainder
+// (|r| <= 2^-9 |x|) is rounded to FP32 once, so the levels carry the value to
+// about 2^-25 relative with two FP64 operations per element.
+template <int NS>
+__device__ __forceinline__ void store_split_f64(__nv_bfloat16* p, long long lo, double x) {
+  const __nv_bfloat16 h0 = __double2bfloat16(x);
+  p[0] = h0;
+  store_split_f32<NS - 1>(p + lo, lo, __double2float_rn(x - (double)__bfloat162float(h0)));
+}
+
 template <int IN, int OUT>
 __global__ void __launch_bounds__(256) gather_kernel(const GItem* __restrict__ items,
                                                      const GContrib* __restrict__ cs, Bases bs) {
   const GItem it = items[blockIdx.x];
-  const long long total = (long long)it.rows * it.cols;
-  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
-    const int r = (int)(e / it.cols), c = (int)(e % it.cols);
-    double acc = 0.0;
-    for (int k = it.c0; k < it.c1; ++k) {
-      const GContrib cb = cs[k];
-      const long long so = (long long)r * cb.src_rs + c;
-      double v;
-      if (IN == 0) v = rptr<const double>(bs, cb.src)[so];
-      else v = (double)rptr<const float>(bs, cb.src)[so];
-      acc = fma(cb.coef, v, acc);
-    }
-    const long long d = (long long)r * it.dst_rs + c;
-    if (OUT == 0) {
-      rptr<double>(bs, it.dst)[d] = acc;
-    } else if (OUT == 1) {
-      rptr<float>(bs, it.dst)[d] = (float)acc;
-    } else {
-      // OUT = 2 / 3: split into OUT bf16 levels
-      __nv_bfloat16* p = rptr<__nv_bfloat16>(bs, it.dst) + d;
-      const long long lo = bs.lo[slot_of(it.dst)];
-      double rem = acc;
-#pragma unroll
-      for (int l = 0; l < OUT; ++l) {
-        __nv_bfloat16 h = __double2bfloat16(rem);
-        p[l * lo] = h;
-        rem -= (double)__bfloat162float(h);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int r = ty; r < it.rows; r += 8)
+    for (int c = tx; c < it.cols; c += 32) {
+      const long long d = (long long)r * it.dst_rs + c;
+      if constexpr (IN == 0) {
+        double acc = 0.0;
+        for (int k = it.c0; k < it.c1; ++k) {
+          const GContrib cb = cs[k];
+          acc = fma(cb.coef, rptr<const double>(bs, cb.src)[(long long)r * cb.src_rs + c], acc);
+        }
+        if constexpr (OUT == 0) rptr<double>(bs, it.dst)[d] = acc;
+        else if constexpr (OUT == 1) rptr<float>(bs, it.dst)[d] = (float)acc;
+        else store_split_f64<OUT>(rptr<__nv_bfloat16>(bs, it.dst) + d, bs.lo[slot_of(it.dst)], acc);
+      } else {
+        float acc = 0.f;
+        for (int k = it.c0; k < it.c1; ++k) {
+          const GContrib cb = cs[k];
+          acc = fmaf((float)cb.coef, rptr<const float>(bs, cb.src)[(long long)r * cb.src_rs + c], acc);
+        }
+        if constexpr (OUT == 0) rptr<double>(bs, it.dst)[d] = (double)acc;
+        else if constexpr (OUT == 1) rptr<float>(bs, it.dst)[d] = acc;
+        else store_split_f32<OUT>(rptr<__nv_bfloat16>(bs, it.dst) + d, bs.lo[slot_of(it.dst)], acc);
       }
     }
-  }
 }
 
-// Strided 2D copy, FP64.
-__global__ void __launch_bounds__(256) copy_kernel(const CItem* __restrict__ items, Bases bs) {
-  const CItem it = items[blockIdx.x];
-  const double* src = rptr<const double>(bs, it.src);
-  double* dst = rptr<double>(bs, it.dst);
-  const long long total = (long long)it.rows * it.cols;
-  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
-    long long r, c;
-    if (it.dst_cs == 1) { r = e / it.cols; c = e % it.cols; } else { c = e / it.rows; r = e % it.rows; }
-    dst[r * it.dst_rs + c * it.dst_cs] = src[r * it.src_rs + c * it.src_cs];
-  }
-}
-
-// Strided FP64 -> split-bf16 copy: levels at dst + l * lo[slot(dst)].
+// Strided 2-D copies, one item = rows x cols elements with arbitrary row and
+// column strides on both sides.  The item is cut into 32 x 32 tiles; the
+// CTAs of grid row blockIdx.x share item blockIdx.x's tiles (stride
+// gridDim.y).  A tile goes through shared memory so that both the load and
+// the store run along whichever side has unit stride (a transposing copy is
+// coalesced on both ends).  NS = 0: FP64 -> FP64; NS = 2, 3: FP64 -> split
+// bf16 levels at dst + l * lo[slot(dst)].
 template <int NS>
-__global__ void __launch_bounds__(256) split_copy_kernel(const CItem* __restrict__ items, Bases bs) {
+__global__ void __launch_bounds__(256) tile_copy_kernel(const CItem* __restrict__ items, Bases bs) {
+  __shared__ double tile[32][33];
   const CItem it = items[blockIdx.x];
   const double* src = rptr<const double>(bs, it.src);
-  __nv_bfloat16* dst = rptr<__nv_bfloat16>(bs, it.dst);
-  const long long lo = bs.lo[slot_of(it.dst)];
-  const long long total = (long long)it.rows * it.cols;
-  for (long long e = threadIdx.x; e < total; e += blockDim.x) {
-    long long r, c;
-    if (it.dst_cs == 1) { r = e / it.cols; c = e % it.cols; } else { c = e / it.rows; r = e % it.rows; }
-    double rem = src[r * it.src_rs + c * it.src_cs];
-    const long long o = r * it.dst_rs + c * it.dst_cs;
+  const int tcr = (it.rows + 31) >> 5, tcc = (it.cols + 31) >> 5;
+  const int ntiles = tcr * tcc;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const bool src_rmaj = it.src_cs == 1 || it.src_rs != 1;   // src contiguous along c
+  const bool dst_rmaj = it.dst_cs == 1 || it.dst_rs != 1;
+  for (int t = blockIdx.y; t < ntiles; t += gridDim.y) {
+    const int r0 = (t / tcc) << 5, c0 = (t % tcc) << 5;
 #pragma unroll
-    for (int l = 0; l < NS; ++l) {
-      const __nv_bfloat16 h = __double2bfloat16(rem);
-      dst[l * lo + o] = h;
-      rem -= (double)__bfloat162float(h);
+    for (int k = 0; k < 4; ++k) {
+      const int a = ty + 8 * k;  // slow index within the tile
+      const int r = src_rmaj ? r0 + a : r0 + tx, c = src_rmaj ? c0 + tx : c0 + a;
+      if (r < it.rows && c < it.cols) {
+        const double v = src[(long long)r * it.src_rs + (long long)c * it.src_cs];
+        if (src_rmaj) tile[a][tx] = v;
+        else tile[tx][a] = v;
+      }
     }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int a = ty + 8 * k;
+      const int lr = dst_rmaj ? a : tx, lc = dst_rmaj ? tx : a;
+      const int r = r0 + lr, c = c0 + lc;
+      if (r < it.rows && c < it.cols) {
+        const long long o = (long long)r * it.dst_rs + (long long)c * it.dst_cs;
+        const double v = tile[lr][lc];
+        if constexpr (NS == 0) rptr<double>(bs, it.dst)[o] = v;
+        else store_split_f64<NS>(rptr<__nv_bfloat16>(bs, it.dst) + o, bs.lo[slot_of(it.dst)], v);
+      }
+    }
+    __syncthreads();
   }
 }
 
-// x (FP64, n) -> ns bf16 levels out[l * n + i], x ~ sum_l out[l]
+static dim3 copy_grid(const DevCopy& c) {
+  // enough CTAs per item for about four tiles each, at most 256 per item
+  const int y = std::max(1, std::min(256, (c.maxtiles + 3) / 4));
+  return dim3((unsigned)c.nitems, (unsigned)y);
+}
+
+// x (FP64, n) -> ns bf16 levels out[l * n + i], x ~ sum_l out[l].
 __global__ void split_bf16_kernel(const double* __restrict__ x, long long n, int ns, __nv_bfloat16* __restrict__ out) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double rem = x[i];
-    for (int l = 0; l < ns; ++l) {
-      __nv_bfloat16 h = __double2bfloat16(rem);
-      out[l * n + i] = h;
-      rem -= (double)__bfloat162float(h);
-    }
+    if (ns == 2) store_split_f64<2>(out + i, n, x[i]);
+    else store_split_f64<3>(out + i, n, x[i]);
   }
 }
 
@@ -602,8 +632,9 @@ constexpr int QRT = 256;
 constexpr int QR_MAXN = 2048;
 
 __global__ void __launch_bounds__(QRT) qr_kernel(const QrJob* __restrict__ jobs, double* __restrict__ ws,
-                                                 const int* __restrict__ only) {
+                                                 const int* __restrict__ only, int* __restrict__ nrun) {
   if (only && !only[blockIdx.x]) return;  // masked launch: fallback sectors only
+  if (nrun && threadIdx.x == 0) atomicAdd(nrun, 1);
   const QrJob J = jobs[blockIdx.x];
   const int m = J.m, n = J.n;
   double* A = ws + J.a;
@@ -797,7 +828,7 @@ cudaError_t launch_gather(const DevGather& g, const Bases& b, int in_type, int o
 
 cudaError_t launch_copy(const DevCopy& c, const Bases& b, cudaStream_t s) {
   if (c.nitems == 0) return cudaSuccess;
-  copy_kernel<<<c.nitems, 256, 0, s>>>(c.items, b);
+  tile_copy_kernel<0><<<copy_grid(c), 256, 0, s>>>(c.items, b);
   return cudaGetLastError();
 }
 
@@ -811,8 +842,8 @@ cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s) { return cudaMems
 
 cudaError_t launch_split_copy(const DevCopy& c, const Bases& b, int nsplit, cudaStream_t s) {
   if (c.nitems == 0) return cudaSuccess;
-  if (nsplit == 2) split_copy_kernel<2><<<c.nitems, 256, 0, s>>>(c.items, b);
-  else if (nsplit == 3) split_copy_kernel<3><<<c.nitems, 256, 0, s>>>(c.items, b);
+  if (nsplit == 2) tile_copy_kernel<2><<<copy_grid(c), 256, 0, s>>>(c.items, b);
+  else if (nsplit == 3) tile_copy_kernel<3><<<copy_grid(c), 256, 0, s>>>(c.items, b);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
@@ -890,13 +921,13 @@ cudaError_t launch_scale_rc(double* a, long long ld, int rows, int cols, const d
 
 cudaError_t launch_qr(const QrJob* jobs, int njobs, double* ws, cudaStream_t s) {
   if (njobs == 0) return cudaSuccess;
-  qr_kernel<<<njobs, QRT, 0, s>>>(jobs, ws, nullptr);
+  qr_kernel<<<njobs, QRT, 0, s>>>(jobs, ws, nullptr, nullptr);
   return cudaGetLastError();
 }
 
-cudaError_t launch_qr_masked(const QrJob* jobs, int njobs, double* ws, const int* only, cudaStream_t s) {
+cudaError_t launch_qr_masked(const QrJob* jobs, int njobs, double* ws, const int* only, int* nrun, cudaStream_t s) {
   if (njobs == 0) return cudaSuccess;
-  qr_kernel<<<njobs, QRT, 0, s>>>(jobs, ws, only);
+  qr_kernel<<<njobs, QRT, 0, s>>>(jobs, ws, only, nrun);
   return cudaGetLastError();
 }
 
@@ -909,18 +940,71 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const CholJob* __restrict
                                                        int* __restrict__ fail) {
   const CholJob J = jobs[blockIdx.x];
   const int n = J.n;
-  double* G = ws + J.g;
-  double* R = ws + J.r;
-  double* Ri = ws + J.ri;
-  __shared__ double piv;
-  __shared__ int bad;
   if (J.shift == 3) {  // more columns than rows: left to the Householder kernel
     if (threadIdx.x == 0) fail[J.sec] = 1;
     return;
   }
+  if (fail[J.sec]) return;  // an earlier pass already gave up on this sector
+  double* G = ws + J.g;
+  double* R = ws + J.r;
+  double* Ri = ws + J.ri;
+  const long long nn = (long long)n * n;
+  __shared__ double piv, red[8];
+  __shared__ int bad;
+  // G = sum of the partial Gram matrices (upper triangle only is used)
+  if (J.parts > 1)
+    for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+      if (e % n < e / n) continue;
+      double acc = G[e];
+      for (int s = 1; s < J.parts; ++s) acc += G[s * nn + e];
+      G[e] = acc;
+    }
+  __syncthreads();
+  if (J.shift == 2) {
+    // Last pass: G = I + E with E small.  Far from the identity means the
+    // earlier passes met a numerically rank-deficient block: Householder
+    // fallback.  When n max|E| <= 1e-8 the factor is I + F to first order,
+    // F = strict upper part of E + diag(E) / 2, and its inverse I - F; the
+    // neglected terms are O(|E|^2), below FP64 rounding.
+    double mx = 0.0;
+    for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int i = (int)(e / n), j = (int)(e % n);
+      if (j < i) continue;
+      const double dev = fabs(G[e] - (i == j ? 1.0 : 0.0));
+      mx = (dev <= mx) ? mx : (dev == dev ? dev : 1e300);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    double all = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) all = fmax(all, red[q]);
+    if (!(all <= 1e-3)) {
+      if (threadIdx.x == 0) fail[J.sec] = 1;
+      return;
+    }
+    if ((double)n * all <= 1e-8) {
+      for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        if (j < i) {
+          R[e] = 0.0;
+          Ri[e] = 0.0;
+        } else if (j == i) {
+          const double h = 0.5 * (G[e] - 1.0);
+          R[e] = 1.0 + h;
+          Ri[e] = 1.0 - h;
+        } else {
+          R[e] = G[e];
+          Ri[e] = -G[e];
+        }
+      }
+      return;
+    }
+  }
   if (threadIdx.x == 0) {
-    bad = fail[J.sec];
-    if (J.shift == 1 && !bad) {
+    bad = 0;
+    if (J.shift == 1) {
+      // shift s = 11 (m n + n (n + 1)) u ||X||^2 with ||X||^2 <= tr(G)
+      // (shifted CholeskyQR, Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020)
       double tr = 0.0;
       for (int i = 0; i < n; ++i) tr += G[(long long)i * n + i];
       const double sft = 11.0 * ((double)J.m * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * tr;
@@ -928,24 +1012,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const CholJob* __restrict
     }
   }
   __syncthreads();
-  if (bad) return;
-  if (J.shift == 2) {
-    // Third pass: its input should already be orthonormal to working
-    // accuracy; a Gram matrix far from the identity means the first two
-    // passes met a (numerically) rank-deficient block, which the Householder
-    // fallback handles instead.
-    int off = 0;
-    for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
-      const int i = (int)(e / n), j = (int)(e % n);
-      const double dev = G[e] - (i == j ? 1.0 : 0.0);
-      if (!(fabs(dev) <= 1e-3)) off = 1;
-    }
-    if (__syncthreads_or(off)) {
-      if (threadIdx.x == 0) fail[J.sec] = 1;
-      return;
-    }
-  }
-  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) R[e] = 0.0;
+  for (long long e = threadIdx.x; e < nn; e += blockDim.x) R[e] = 0.0;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {

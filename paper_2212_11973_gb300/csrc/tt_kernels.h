@@ -33,6 +33,7 @@ struct DevGather {
 struct DevCopy {
   CItem* items = nullptr;
   int nitems = 0;
+  int maxtiles = 0;  // largest item, in 32 x 32 tiles
 };
 
 // Device-side Krylov bookkeeping of one Lanczos exponential.
@@ -97,7 +98,9 @@ cudaError_t k_normalise_inplace(double* v, int64_t n, double* partial, KrylovSta
 // Householder QR of a batch of column-major matrices in workspace `ws`.
 cudaError_t launch_qr(const QrJob* jobs, int njobs, double* ws, cudaStream_t s);
 // the same, only for the jobs whose only[job] != 0
-cudaError_t launch_qr_masked(const QrJob* jobs, int njobs, double* ws, const int* only, cudaStream_t s);
+// Householder QR of the jobs whose flag in `only` is set; *nrun (if not null)
+// counts the sectors factorised.
+cudaError_t launch_qr_masked(const QrJob* jobs, int njobs, double* ws, const int* only, int* nrun, cudaStream_t s);
 // Cholesky + triangular inverse per job (shifted on request); fail[sec] set on
 // a non-positive pivot.
 cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s);

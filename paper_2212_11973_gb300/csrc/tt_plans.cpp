@@ -285,29 +285,51 @@ CopyPlan build_env_split(const Bond& B, const std::vector<Q>& chan) {
 }
 
 BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed) {
+  // y_q = sum_w L_w(q <- b) x_b R_w(q <- b)^T with b = q - ch[w]: first
+  // T_b = L_b x_b for all channels at once (rows (w, a) of the environment),
+  // then per output sector the sum over w of (rows of channel w of T_b) R^T.
   BondPlanHost P;
   EnvLayout E = make_env_layout(B, ch);
   EnvLayout Eo = make_env_layout(B, ch, mixed);  // operand layout of L and R
   P.mat = make_bondmat_layout(B);
   const int nw = (int)ch.size();
-  std::vector<int64_t> toff(B.nsec(), -1);
-  int64_t cur = 0;
+  std::vector<int64_t> toff(B.nsec(), -1), tpoff(B.nsec(), -1), xtoff(B.nsec(), 0);
+  int64_t cur = 0, curp = 0, xt = 0;
   for (int b = 0; b < B.nsec(); ++b) {
+    const int d = B.dim[b], ldp = pad8i(d);
+    if (mixed) {
+      xtoff[b] = xt;
+      P.xsplit.items.push_back(CItem{mkref(S_X, P.mat.off[b]), mkref(S_Y, xt), d, 1, 1, ldp, d, d});
+      xt += (int64_t)d * ldp;
+    }
     if (E.rows[b] == 0) continue;
     toff[b] = cur;
-    P.b1.add_group((int)E.rows[b], B.dim[b], mkref(S_T1, cur), B.dim[b], 0);
-    P.b1.add_seg(mkref(S_L, Eo.off[b]), Eo.ld[b], 0, mkref(S_X, P.mat.off[b]), B.dim[b], 0, B.dim[b]);
-    cur += E.rows[b] * B.dim[b];
+    P.b1.add_group((int)E.rows[b], d, mkref(S_T1, cur), d, 0);
+    if (mixed) {
+      P.b1.add_seg(mkref(S_L, Eo.off[b]), Eo.ld[b], 0, mkref(S_X, xtoff[b]), ldp, 1, d);
+      tpoff[b] = curp;
+      P.tsplit.items.push_back(CItem{mkref(S_T1, cur), mkref(S_Y, curp), d, 1, ldp, 1, (int)E.rows[b], d});
+      curp += E.rows[b] * ldp;
+    } else {
+      P.b1.add_seg(mkref(S_L, Eo.off[b]), Eo.ld[b], 0, mkref(S_X, P.mat.off[b]), d, 0, d);
+    }
+    cur += E.rows[b] * d;
   }
   P.t_size = cur;
+  P.xt_size = pad8l(xt);
+  P.tp_size = pad8l(curp);
   for (int q = 0; q < B.nsec(); ++q) {
     P.b2.add_group(B.dim[q], B.dim[q], mkref(S_Y, P.mat.off[q]), B.dim[q], 0);
     for (int w = 0; w < nw; ++w) {
       int b = B.find(B.q[q] - ch[w]);
       if (b < 0 || toff[b] < 0) continue;
       int64_t row = E.row_of(b, w);
-      P.b2.add_seg(mkref(S_T2, toff[b] + row * B.dim[b]), B.dim[b], 0, mkref(S_R, Eo.off[b] + row * Eo.ld[b]),
-                   Eo.ld[b], 1, B.dim[b]);
+      if (mixed)
+        P.b2.add_seg(mkref(S_T2, tpoff[b] + row * pad8i(B.dim[b])), pad8i(B.dim[b]), 0,
+                     mkref(S_R, Eo.off[b] + row * Eo.ld[b]), Eo.ld[b], 1, B.dim[b]);
+      else
+        P.b2.add_seg(mkref(S_T2, toff[b] + row * B.dim[b]), B.dim[b], 0, mkref(S_R, Eo.off[b] + row * Eo.ld[b]),
+                     Eo.ld[b], 1, B.dim[b]);
     }
   }
   return P;
@@ -417,28 +439,50 @@ QrPlanHost build_lq_right(const SiteLayout& S, const Bond& BL, bool shrink) {
 }
 
 CholQrPlan build_cholqr(const std::vector<QrJob>& jobs, int64_t ws0) {
+  // Per sector (m x n, column-major X):
+  //   G = X^T X: only the upper block triangle (row blocks of 64, columns from
+  //   the block's first row on), K split into `parts` chunks that write
+  //   separate partial Gram matrices (summed by the Cholesky kernel);
+  //   Xo^T = RI^T X^T: RI is upper triangular, so output row block q0 needs
+  //   K = min(n, q0 + 64) only.
+  constexpr int RB = 64, KCHUNK = 512, MAXPARTS = 16;
   CholQrPlan P;
   int64_t w = ws0;
   for (size_t sec = 0; sec < jobs.size(); ++sec) {
     const QrJob& J = jobs[sec];
     const int m = J.m, n = J.n;
     if (m < n || n == 0) {  // rank-deficient by shape: Householder only
-      if (n > 0) P.cj[0].push_back(CholJob{0, 0, 0, m, n, 3, (int)sec});
+      if (n > 0) P.cj[0].push_back(CholJob{0, 0, 0, m, n, 3, (int)sec, 1});
       continue;
     }
+    const int parts = std::max(1, std::min(MAXPARTS, (m + KCHUNK - 1) / KCHUNK));
+    int kc = (m + parts - 1) / parts;
+    kc = (kc + 15) / 16 * 16;
     const int64_t mn = (int64_t)m * n, nn = (int64_t)n * n;
-    const int64_t q0 = w, q1 = q0 + mn, g = q1 + mn, r0 = g + nn, r1 = r0 + nn, r2 = r1 + nn, ri0 = r2 + nn,
-                  ri1 = ri0 + nn, ri2 = ri1 + nn, tt = ri2 + nn;
+    const int64_t q0 = w, q1 = q0 + mn, g = q1 + mn, r0 = g + parts * nn, r1 = r0 + nn, r2 = r1 + nn,
+                  ri0 = r2 + nn, ri1 = ri0 + nn, ri2 = ri1 + nn, tt = ri2 + nn;
     w = tt + nn;
     const int64_t X[3] = {J.a, q0, q1}, Xo[3] = {q0, q1, J.q}, R[3] = {r0, r1, r2}, RI[3] = {ri0, ri1, ri2};
     for (int p = 0; p < 3; ++p) {
-      // G = X^T X : A = X^T (row-major n x m, ld m), B = X stored N x K (ld m)
-      P.gram[p].add_group(n, n, mkref(S_AUX2, g), n, 0);
-      P.gram[p].add_seg(mkref(S_AUX2, X[p]), m, 0, mkref(S_AUX2, X[p]), m, 1, m);
-      P.cj[p].push_back(CholJob{g, R[p], RI[p], m, n, p == 0 ? 1 : (p == 2 ? 2 : 0), (int)sec});
-      // Xo^T = RI^T X^T : written row-major (n x m) = Xo column-major
-      P.app[p].add_group(n, m, mkref(S_AUX2, Xo[p]), m, 0);
-      P.app[p].add_seg(mkref(S_AUX2, RI[p]), n, 1, mkref(S_AUX2, X[p]), m, 0, n);
+      for (int s = 0; s < parts; ++s) {
+        const int k0 = s * kc, K = std::min(kc, m - k0);
+        if (K <= 0) {  // empty chunk: its partial must still be written
+          for (int i0 = 0; i0 < n; i0 += RB)
+            P.gram[p].add_group(std::min(RB, n - i0), n - i0, mkref(S_AUX2, g + s * nn + (int64_t)i0 * n + i0), n, 0);
+          continue;
+        }
+        for (int i0 = 0; i0 < n; i0 += RB) {
+          P.gram[p].add_group(std::min(RB, n - i0), n - i0, mkref(S_AUX2, g + s * nn + (int64_t)i0 * n + i0), n, 0);
+          const Ref xa = mkref(S_AUX2, X[p] + (int64_t)i0 * m + k0);
+          P.gram[p].add_seg(xa, m, 0, xa, m, 1, K);
+        }
+      }
+      const int shift = p == 0 ? 1 : (p == 2 ? 2 : 0);
+      P.cj[p].push_back(CholJob{g, R[p], RI[p], m, n, shift, (int)sec, parts});
+      for (int r0b = 0; r0b < n; r0b += RB) {
+        P.app[p].add_group(std::min(RB, n - r0b), m, mkref(S_AUX2, Xo[p] + (int64_t)r0b * m), m, 0);
+        P.app[p].add_seg(mkref(S_AUX2, RI[p] + r0b), n, 1, mkref(S_AUX2, X[p]), m, 0, std::min(n, r0b + RB));
+      }
     }
     // T^T = R0^T R1^T ; R^T = T^T R2^T (row-major R^T = column-major R)
     P.tt.add_group(n, n, mkref(S_AUX2, tt), n, 0);

@@ -22,6 +22,10 @@ struct BondPlanHost {
   BondMatLayout mat;
   GemmPlan b1, b2;
   int64_t t_size = 0;
+  // mixed precision: B1's B operand is the transposed split of x (rows padded
+  // to 8), B2's A operand the split of T with rows padded to 8
+  CopyPlan xsplit, tsplit;
+  int64_t xt_size = 0, tp_size = 0;
 };
 
 struct QrPlanHost {

@@ -282,9 +282,13 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
     }
     __syncthreads();
   } else {
-    // epilogue: row = tid
-    const int row = tl.m0 + tid;
+    // epilogue: TMEM lane = tile row = tid.  Each 32-column slice goes through
+    // shared memory (the idle stage buffers) so that a warp stores 32
+    // consecutive columns of one row per instruction.
     const bool accum = g.flags & 1, out_f32 = g.flags & 2;
+    float* stg = reinterpret_cast<float*>(smem);     // [128][33]
+    double* stgd = reinterpret_cast<double*>(smem);  // [128][33]
+    const int lane = tid & 31;
 #pragma unroll 1
     for (int cb = 0; cb < TBN; cb += 32) {
       if (folds > 0) {
@@ -294,23 +298,31 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
 #pragma unroll
         for (int i = 0; i < 32; ++i) { h[i] = 0.f; w[i] = 0.f; }
       }
-      if (row < g.M) {
+      if (out_f32) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = tl.n0 + cb + i;
-          if (col < g.N) {
-            const double val = (double)h[i] + (double)w[i];
-            const long long o = (long long)row * g.ldc + col;
-            if (out_f32) {
-              float* C = reinterpret_cast<float*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
-              *C = accum ? *C + (float)val : (float)val;
-            } else {
-              double* C = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
-              *C = accum ? *C + val : val;
-            }
+        for (int i = 0; i < 32; ++i) stg[tid * 33 + i] = h[i] + w[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) stgd[tid * 33 + i] = (double)h[i] + (double)w[i];
+      }
+      __syncthreads();
+      const int col = tl.n0 + cb + lane;
+      for (int rr = warp; rr < TBM; rr += 4) {
+        const int row = tl.m0 + rr;
+        if (row < g.M && col < g.N) {
+          const long long o = (long long)row * g.ldc + col;
+          if (out_f32) {
+            float* C = reinterpret_cast<float*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+            const float val = stg[rr * 33 + lane];
+            *C = accum ? *C + val : val;
+          } else {
+            double* C = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+            const double val = stgd[rr * 33 + lane];
+            *C = accum ? *C + val : val;
           }
         }
       }
+      __syncthreads();
     }
   }
   fence_before();
@@ -329,20 +341,16 @@ cudaError_t launch_gemm_tc(const GGroup* groups, const GSeg* segs, const GTile* 
   if (ntiles == 0) return cudaSuccess;
   const size_t smem = tc_smem_bytes(nsplit);
   if (nsplit == 2) {
-    static bool set2 = false;
-    if (!set2) {
-      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      set2 = true;
-    }
+    // once per process (thread-safe static initialisation)
+    static const cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)smem);
+    if (e != cudaSuccess) return e;
     gemm_tc_kernel<2><<<ntiles, 128, smem, s>>>(groups, segs, tiles128, (const CUtensorMap*)maps, b, err);
   } else if (nsplit == 3) {
-    static bool set3 = false;
-    if (!set3) {
-      cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      set3 = true;
-    }
+    // once per process (thread-safe static initialisation)
+    static const cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)smem);
+    if (e != cudaSuccess) return e;
     gemm_tc_kernel<3><<<ntiles, 128, smem, s>>>(groups, segs, tiles128, (const CUtensorMap*)maps, b, err);
   } else {
     return cudaErrorInvalidValue;

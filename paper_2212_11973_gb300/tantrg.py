@@ -61,7 +61,9 @@ class tt_stats(C.Structure):
                 ("gather_ms", C.c_double), ("gather_launches", C.c_longlong),
                 ("step_flops", C.c_double), ("step_ms", C.c_double), ("launches", C.c_longlong),
                 ("n_sites", C.c_int), ("max_bond", C.c_int), ("n_sectors_max", C.c_int),
-                ("qr_ms", C.c_double)]
+                ("qr_ms", C.c_double), ("bond_flops", C.c_double), ("qr_sectors", C.c_longlong), ("qr_fallbacks", C.c_longlong),
+                ("site_exp_ms", C.c_double), ("bond_exp_ms", C.c_double), ("env_update_ms", C.c_double),
+                ("absorb_ms", C.c_double), ("gauge_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,12 +92,22 @@ SIGNATURES = {
     "tt_stats_get": (C.c_int, [_P, C.POINTER(tt_stats)]),
     "tt_rho_set_profiling": (C.c_int, [_P, C.c_int]),
     "tt_rho_bond_dims": (C.c_int, [_P, _PI, C.c_int]),
+    "tt_rho_bond_sectors": (C.c_int, [_P, C.c_int, _PI, _PI, _PI, C.c_int, _PI]),
     "tt_rho_save": (C.c_int, [_P, C.c_char_p]),
     "tt_rho_load": (C.c_int, [_P, _P, C.c_char_p, C.POINTER(tt_run_opts), C.POINTER(_P)]),
     "tt_layout_sizes": (C.c_int, [_P, C.c_int, _PI, _PI, _PI, _PI, _PL, _PL, _PL]),
     "tt_heff_apply_host": (C.c_int, [_P, _P, C.c_int, C.c_int, _PI, _PI, _PI, _PI, _PD, _PD, _PD, _PD]),
     "tt_qr_device": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
     "tt_qr_device_noalloc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
+    "tt_batch_create": (C.c_int, [_P, C.c_int, C.POINTER(tt_model), _PI, C.c_double, C.POINTER(tt_run_opts),
+                                  C.POINTER(_P)]),
+    "tt_batch_destroy": (None, [_P]),
+    "tt_batch_size": (C.c_int, [_P]),
+    "tt_batch_grow": (C.c_int, [_P, C.c_double, C.c_double]),
+    "tt_batch_step": (C.c_int, [_P, C.c_double, C.c_int]),
+    "tt_batch_measure": (C.c_int, [_P, C.POINTER(tt_obs)]),
+    "tt_batch_stats": (C.c_int, [_P, C.c_int, C.POINTER(tt_stats)]),
+    "tt_batch_set_profiling": (C.c_int, [_P, C.c_int]),
 }
 
 _lib = None
@@ -253,6 +265,16 @@ class Rho:
         _check(self.ctx.h, load_library().tt_rho_bond_dims(self.h, arr, n))
         return list(arr)
 
+    def bond_sectors(self, k):
+        """[(n, s, dim)] of bond k: particle number and n_up - n_dn charges."""
+        lib = load_library()
+        ns = C.c_int(0)
+        lib.tt_rho_bond_sectors(self.h, k, None, None, None, 0, C.byref(ns))
+        n = ns.value
+        qn, qs, dd = (C.c_int * max(n, 1))(), (C.c_int * max(n, 1))(), (C.c_int * max(n, 1))()
+        _check(self.ctx.h, lib.tt_rho_bond_sectors(self.h, k, qn, qs, dd, n, C.byref(ns)))
+        return [(qn[i], qs[i], dd[i]) for i in range(n)]
+
     def save(self, path):
         _check(self.ctx.h, load_library().tt_rho_save(self.h, path.encode()))
 
@@ -326,3 +348,50 @@ def qr_device_noalloc(A, Q, R, stream=None):
                                                  C.c_void_p(R.data_ptr()), C.c_void_p(st))
     if status != TT_OK:
         raise TTError(status, "tt_qr_device_noalloc failed (sizes beyond the fixed scratch, or a CUDA error)")
+
+
+class Batch:
+    """Independent instances stepped together (tt_batch_*): workloads is a list
+    of objects with Lx, Wy, periodic, t, U, mu, form, D; opts gives the rest."""
+
+    def __init__(self, ctx: Context, workloads, beta0: float, opts: tt_run_opts):
+        lib = load_library()
+        self.ctx = ctx
+        n = len(workloads)
+        self.n = n
+        models = (tt_model * n)(*[tt_model(w.Lx, w.Wy, int(w.periodic), w.t, 0.0, w.U, w.mu, w.form)
+                                  for w in workloads])
+        dmax = (C.c_int * n)(*[w.D for w in workloads])
+        h = C.c_void_p()
+        _check(ctx.h, lib.tt_batch_create(ctx.h, n, models, dmax, beta0, C.byref(opts), C.byref(h)))
+        self.h = h
+
+    def grow(self, dtau, beta_max):
+        _check(self.ctx.h, load_library().tt_batch_grow(self.h, dtau, beta_max))
+
+    def step(self, dtau, n_steps=1):
+        _check(self.ctx.h, load_library().tt_batch_step(self.h, dtau, n_steps))
+
+    def measure(self):
+        obs = (tt_obs * self.n)()
+        _check(self.ctx.h, load_library().tt_batch_measure(self.h, obs))
+        return [o.as_dict() for o in obs]
+
+    def set_profiling(self, on: bool):
+        _check(self.ctx.h, load_library().tt_batch_set_profiling(self.h, int(on)))
+
+    def stats(self, i) -> dict:
+        s = tt_stats()
+        _check(self.ctx.h, load_library().tt_batch_stats(self.h, i, C.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().tt_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

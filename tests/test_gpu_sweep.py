@@ -35,12 +35,12 @@ def ctx(tt):
     c.close()
 
 
-def _gpu_run(tt, ctx, cfg, beta_end, precision=None, D=None):
+def _gpu_run(tt, ctx, cfg, beta_end, precision=None, D=None, grow_until=1.0):
     mpo = tt.Mpo(ctx, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
     D = D or cfg.D
     prec = cfg.precision if precision is None else precision
     rho = tt.Rho(ctx, mpo, cfg.beta0, tt.run_opts(D, cfg.krylov, prec))
-    rho.grow(cfg.dtau, min(1.0, beta_end))  # the oracle also stops growing at beta_end
+    rho.grow(cfg.dtau, min(grow_until, beta_end))  # the oracle's switch rule, same grow_until
     obs = [rho.measure()]
     while obs[-1]["beta"] < beta_end - 1e-9:
         rho.step(cfg.dtau, 1)
@@ -51,7 +51,7 @@ def _gpu_run(tt, ctx, cfg, beta_end, precision=None, D=None):
     return obs, dims
 
 
-def _oracle_run(cfg, beta_end, D=None):
+def _oracle_run(cfg, beta_end, D=None, grow_until=1.0):
     from oracle import model as om
     from oracle import mpo as ompo
     from oracle import tantrg as ot
@@ -61,7 +61,8 @@ def _oracle_run(cfg, beta_end, D=None):
     def cb(st, stage):
         rec[round(st.beta, 9)] = ot.measure(st)
 
-    st = ot.run(ompo.hubbard_mpo(m), cfg.beta0, cfg.dtau, beta_end, ot.TruncOpts(D or cfg.D), K=cfg.krylov, callback=cb)
+    st = ot.run(ompo.hubbard_mpo(m), cfg.beta0, cfg.dtau, beta_end, ot.TruncOpts(D or cfg.D), K=cfg.krylov,
+                grow_until=grow_until, callback=cb)
     return rec, st
 
 
@@ -89,10 +90,12 @@ def test_cluster_2x2_untruncated_matches_oracle(tt, ctx):
 
 
 def test_ladder_fp64_matches_oracle(tt, ctx):
-    """2x4 ladder at D = 32: several sectors per bond, truncated growth."""
+    """2x4 ladder at D = 32: several sectors per bond, truncated growth to
+    beta = 0.2, then 1-TDVP steps to 0.51 on both sides."""
     cfg = wl.LADDER_2x4
-    gpu, dims = _gpu_run(tt, ctx, cfg, 0.51)
-    ref, st = _oracle_run(cfg, 0.51)
+    gpu, dims = _gpu_run(tt, ctx, cfg, 0.51, grow_until=0.2)
+    ref, st = _oracle_run(cfg, 0.51, grow_until=0.2)
+    assert len(gpu) >= 6  # the linear stage ran
     assert dims[1:-1] == st.bond_dims()
     for o in gpu:
         r = ref[round(o["beta"], 9)]
@@ -103,8 +106,9 @@ def test_ladder_fp64_matches_oracle(tt, ctx):
 @pytest.mark.parametrize("prec,tol", [(2, 1e-6)])
 def test_ladder_mixed_matches_oracle(tt, ctx, prec, tol):
     cfg = wl.LADDER_2x4
-    gpu, dims = _gpu_run(tt, ctx, cfg, 0.51, precision=prec)
-    ref, st = _oracle_run(cfg, 0.51)
+    gpu, dims = _gpu_run(tt, ctx, cfg, 0.51, precision=prec, grow_until=0.2)
+    ref, st = _oracle_run(cfg, 0.51, grow_until=0.2)
+    assert len(gpu) >= 6  # the linear stage ran in split-BF16
     assert dims[1:-1] == st.bond_dims()
     for o in gpu:
         r = ref[round(o["beta"], 9)]
