@@ -120,10 +120,12 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GGroup* __restrict_
 // accumulation).  Operands are stored as NS bf16 levels x = x0 + x1 (+ x2),
 // level l at element offset l * lo[slot]; the products with l_A + l_B < NS are
 // summed: NS = 2 -> 3 products (~2^-16 relative), NS = 3 -> 6 products
-// (~2^-24).  The FP32 accumulators of every 32-wide K chunk are folded into a
-// two-float (hi, lo) sum with TwoSum (Knuth, TAOCP vol. 2, 4.2.2), so the
-// accumulation error does not grow with K.  64 x 64 tile per CTA, 4 warps of
-// 32 x 32.  Output FP64 or FP32 (flags bit1).
+// (~2^-24).  The leading product x0*y0 and the smaller ones accumulate in
+// separate FP32 registers; every 32-wide K chunk the leading one is folded
+// into a two-float (hi, lo) sum with TwoSum (Knuth, TAOCP vol. 2, 4.2.2) and
+// the small one is added to lo, so the accumulation error does not grow with
+// K.  64 x 64 tile per CTA, 4 warps of 32 x 32.  Output FP64 or FP32 (flags
+// bit1).
 // ---------------------------------------------------------------------------
 constexpr int HBM = 64, HBN = 64, HBK = 32, HPAD = 8;
 
@@ -154,13 +156,13 @@ __global__ void __launch_bounds__(128) gemm_bf16_split_kernel(const GGroup* __re
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
   const int gid = lane >> 2, tig = lane & 3;
-  float acc[2][4][4], hi[2][4][4], lo[2][4][4];
+  float acc[2][4][4], accs[2][4][4], hi[2][4][4], lo[2][4][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) { acc[i][j][r] = 0.f; hi[i][j][r] = 0.f; lo[i][j][r] = 0.f; }
+      for (int r = 0; r < 4; ++r) { acc[i][j][r] = 0.f; accs[i][j][r] = 0.f; hi[i][j][r] = 0.f; lo[i][j][r] = 0.f; }
 
   for (int si = g.seg0; si < g.seg1; ++si) {
     const GSeg sg = segs[si];
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_split_kernel(const GGroup* __re
 #pragma unroll
           for (int i = 0; i < 2; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) mma_bf16_16816(acc[i][j], af[i], bf[j]);
+            for (int j = 0; j < 4; ++j) mma_bf16_16816(order == 0 ? acc[i][j] : accs[i][j], af[i], bf[j]);
         }
       }
       __syncthreads();
@@ -224,7 +226,9 @@ __global__ void __launch_bounds__(128) gemm_bf16_split_kernel(const GGroup* __re
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
             two_sum_acc(hi[i][j][r], lo[i][j][r], acc[i][j][r]);
+            lo[i][j][r] += accs[i][j][r];
             acc[i][j][r] = 0.f;
+            accs[i][j][r] = 0.f;
           }
     }
   }

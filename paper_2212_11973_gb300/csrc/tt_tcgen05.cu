@@ -31,7 +31,13 @@ namespace {
 constexpr int TBM = 128, TBN = 128, TBK = 64;
 constexpr int TILE_BYTES = TBM * TBK * 2;  // 16 KB per level and operand
 constexpr int FOLD = 2;                    // chunks per TMEM fold
-constexpr uint32_t TMEM_COLS = 512;        // acc [0,128), hi [128,256), lo [256,384)
+// TMEM columns: the leading level product hi*hi accumulates in [0,128), the
+// five (x6) or two (x3) smaller products in [128,256); the running two-float
+// sum of the folds is hi [256,384), lo [384,512).  Keeping the small products
+// out of the main accumulator means the FP32 roundings of the tensor-core
+// accumulation act on the dominant term only 4 times per 64-long K chunk
+// instead of 4 * (number of products) times.
+constexpr uint32_t TMEM_COLS = 512;
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ int slot_of(Ref r) { return (int)(r >> 56); }
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_base_s;
-  const uint32_t t_acc = tmem, t_hi = tmem + TBN, t_lo = tmem + 2 * TBN;
+  const uint32_t t_acc = tmem, t_acc2 = tmem + TBN, t_hi = tmem + 2 * TBN, t_lo = tmem + 3 * TBN;
   const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
 
   // instruction descriptor: D f32, A/B bf16, both K-major, N = 128, M = 128
@@ -206,7 +212,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
   int issued = 0;   // TMA chunks issued
   int folds = 0;
   bool ok = true;
-  float v[32], h[32], w[32];
+  float v[32], u[32], h[32], w[32];
   for (int b0 = 0; b0 < total; b0 += FOLD) {
     const int b1 = min(total, b0 + FOLD);
     if (tid == 0) {
@@ -229,8 +235,8 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
           const uint32_t aa = sa + la * TILE_BYTES, ba = sa + (NS + lb) * TILE_BYTES;
 #pragma unroll
           for (int kk = 0; kk < TBK / 16; ++kk) {
-            const uint32_t acc = (c > b0 || p > 0 || kk > 0) ? 1u : 0u;
-            umma_f16(t_acc, make_desc(aa + kk * 32), make_desc(ba + kk * 32), idesc, acc);
+            const uint32_t acc = (c > b0 || p > 1 || kk > 0) ? 1u : 0u;
+            umma_f16(p == 0 ? t_acc : t_acc2, make_desc(aa + kk * 32), make_desc(ba + kk * 32), idesc, acc);
           }
         }
         umma_commit(&empty_bar[s]);
@@ -247,12 +253,12 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
     fence_after();
 #pragma unroll 1
     for (int cb = 0; cb < TBN; cb += 32) {
+      // main part: TwoSum into (hi, lo); small products: added to lo
       tmem_ld32(t_acc + lane_off + cb, v);
+      tmem_ld32(t_acc2 + lane_off + cb, u);
       if (folds == 0) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) w[i] = 0.f;
         tmem_st32(t_hi + lane_off + cb, v);
-        tmem_st32(t_lo + lane_off + cb, w);
+        tmem_st32(t_lo + lane_off + cb, u);
       } else {
         tmem_ld32(t_hi + lane_off + cb, h);
         tmem_ld32(t_lo + lane_off + cb, w);
@@ -261,7 +267,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
           const float s = h[i] + v[i];
           const float bp = s - h[i];
           const float ap = s - bp;
-          w[i] += (h[i] - ap) + (v[i] - bp);
+          w[i] += ((h[i] - ap) + (v[i] - bp)) + u[i];
           h[i] = s;
         }
         tmem_st32(t_hi + lane_off + cb, h);

@@ -42,7 +42,11 @@ def test_save_load_step(tt, tmp_path, prec_saved, prec_loaded, tol):
     r2 = tt.Rho.load(ctx, mpo, path, tt.run_opts(cfg.D, cfg.krylov, prec_loaded))
     loaded = r2.measure()
     for k in KEYS:
-        assert _rel(loaded[k], before[k]) < 1e-12, ("after load", k, loaded[k], before[k])
+        # a loaded state rebuilds its environments in FP64: the energy of a
+        # state saved from the split-BF16 path moves by the environments'
+        # mixed-precision error, everything else is a function of the tensors
+        t = tol if (prec_saved and k == "energy_per_site") else 1e-12
+        assert _rel(loaded[k], before[k]) < t, ("after load", k, loaded[k], before[k])
     rho.step(cfg.dtau, 1)
     r2.step(cfg.dtau, 1)
     a, b = rho.measure(), r2.measure()
