@@ -219,6 +219,8 @@ tt_status tt_batch_create(tt_ctx* ctx, int n, const tt_model* models, const int*
 void tt_batch_destroy(tt_batch* b);
 int tt_batch_size(const tt_batch* b);
 tt_status tt_batch_grow(tt_batch* b, double dtau, double beta_max);
+/* tt_rho_pad of every instance to its own D_max (synchronous). */
+tt_status tt_batch_pad(tt_batch* b);
 tt_status tt_batch_step(tt_batch* b, double dtau, int n_steps);
 tt_status tt_batch_measure(tt_batch* b, tt_obs* out_n);
 /* tt_stats_get of instance i; profiling switched for every instance. */

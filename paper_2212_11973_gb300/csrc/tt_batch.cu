@@ -25,6 +25,7 @@ struct tt_batch {
     tt_ctx* c = nullptr;
     tt_mpo* mpo = nullptr;
     tt_rho* rho = nullptr;
+    int D_max = 0;
   };
   std::vector<Inst> inst;
   cudaEvent_t fork = nullptr;
@@ -101,6 +102,7 @@ tt_status tt_batch_create(tt_ctx* ctx, int n, const tt_model* models, const int*
     if (s != TT_OK) break;
     tt_run_opts o = *opts;
     o.D_max = D_max[i];
+    in.D_max = D_max[i];
     if ((s = tt_hubbard_mpo_create(in.c, &models[i], &in.mpo)) != TT_OK ||
         (s = tt_rho_create(in.c, in.mpo, beta0, 1, &o, &in.rho)) != TT_OK) {
       s = fail_inst(b, i, s);
@@ -129,6 +131,15 @@ tt_status tt_batch_grow(tt_batch* b, double dtau, double beta_max) {
   return for_each_instance(b, [&](size_t i) {
     double reached = 0;
     return tt_rho_grow(b->inst[i].rho, b->inst[i].mpo, dtau, beta_max, &reached);
+  });
+}
+
+tt_status tt_batch_pad(tt_batch* b) {
+  if (!b) return TT_ERR_INVALID_ARG;
+  return for_each_instance(b, [&](size_t i) {
+    tt_status s = tt_rho_pad(b->inst[i].rho, b->inst[i].mpo, b->inst[i].D_max);
+    if (s == TT_OK) s = cudaStreamSynchronize(b->inst[i].st) == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+    return s;
   });
 }
 

@@ -104,6 +104,7 @@ SIGNATURES = {
     "tt_batch_destroy": (None, [_P]),
     "tt_batch_size": (C.c_int, [_P]),
     "tt_batch_grow": (C.c_int, [_P, C.c_double, C.c_double]),
+    "tt_batch_pad": (C.c_int, [_P]),
     "tt_batch_step": (C.c_int, [_P, C.c_double, C.c_int]),
     "tt_batch_measure": (C.c_int, [_P, C.POINTER(tt_obs)]),
     "tt_batch_stats": (C.c_int, [_P, C.c_int, C.POINTER(tt_stats)]),
@@ -368,6 +369,9 @@ class Batch:
 
     def grow(self, dtau, beta_max):
         _check(self.ctx.h, load_library().tt_batch_grow(self.h, dtau, beta_max))
+
+    def pad(self):
+        _check(self.ctx.h, load_library().tt_batch_pad(self.h))
 
     def step(self, dtau, n_steps=1):
         _check(self.ctx.h, load_library().tt_batch_step(self.h, dtau, n_steps))

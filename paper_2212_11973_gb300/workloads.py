@@ -76,6 +76,11 @@ def batch_ladders(n: int = 64, seed: int = BATCH_SEED):
     return out
 
 
+# U(1)xU(1) bond charges (particle number, n_up - n_dn) of the Choi super-MPS
+# within |n|, |s| <= 4; n + s is even for every local pair charge.
+SECTOR_CHARGES = [(n, s) for n in range(-4, 5) for s in range(-4, 5) if (n + s) % 2 == 0]
+
+
 def gaussian_sectors(total: int, width: float, allowed, seed: int = 0):
     """Sector table [(n, 2Sz, dim)] with dims ~ exp(-(n^2 + s^2) / (2 width^2)),
     summing to `total`, over the given allowed charges (sorted)."""

@@ -14,7 +14,7 @@ from paper_2212_11973_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-ALLOWED = [(n, s) for n in range(-4, 5) for s in range(-4, 5) if (n + s) % 2 == 0]
+ALLOWED = wl.SECTOR_CHARGES
 
 
 @pytest.fixture(scope="module")
