@@ -309,9 +309,7 @@ struct Eng {
     s.h = build_site_plan(r->bond[j], r->bond[j + 1], m.ls, m.site[j].terms, m.chan[j], m.chan[j + 1], mixed());
     validate_site(s.h, r->bond[j], r->bond[j + 1], m.chan[j], m.chan[j + 1], mixed());
     upload(c, s.h.xsplit, s.xs);
-    upload(c, s.h.xpad, s.xp);
     if (mixed()) ensure(c, r->Xs, (size_t)std::max<int64_t>(s.h.xt_size, 1) * 2 * r->nsplit);
-    if (mixed()) ensure(c, r->Xp, (size_t)std::max<int64_t>(s.h.xp_size, 1) * 2 * r->nsplit);
     upload(c, s.h.s1, s.s1);
     upload(c, s.h.s2, s.s2);
     upload(c, s.h.s3, s.s3);
@@ -336,11 +334,9 @@ struct Eng {
     check_plan(h.s2, caps({{S_T1, h.t1_size}, {S_T2, h.t2_size}}), "S2");
     check_plan(h.s3, caps({{S_T2, h.t2_size}, {S_R, ero}, {S_Y, n}}), "S3");
     check_plan(h.s3l, caps({{sx, n}, {S_T2, h.t2_size}, {S_Y, er}}), "S3L");
-    const int64_t xpn = mx ? h.xp_size : n;  // R1 / R3: row-padded split copy of x
-    if (mx) check_plan(h.xpad, caps({{S_X, n}, {S_Y, h.xp_size}}), "x pad");
-    check_plan(h.r1, caps({{sx, xpn}, {S_R, ero}, {S_T1, h.u1_size}}), "R1");
+    check_plan(h.r1, caps({{sx, n}, {S_R, ero}, {S_T1, h.u1_size}}), "R1");
     check_plan(h.r2, caps({{S_T1, h.u1_size}, {S_T2, h.u2_size}}), "R2");
-    check_plan(h.r3, caps({{sx, xpn}, {S_T2, h.u2_size}, {S_Y, el}}), "R3");
+    check_plan(h.r3, caps({{sx, n}, {S_T2, h.u2_size}, {S_Y, el}}), "R3");
     if (mx) check_plan(h.xsplit, caps({{S_X, n}, {S_Y, h.xt_size}}), "x split");
   }
 
@@ -789,20 +785,9 @@ struct Eng {
     b.p[S_T1] = r->T1.p;
     b.p[S_T2] = r->T2.p;
     if (mixed()) {
-      const size_t el = 2 * (size_t)r->nsplit;
-      need(r->Xp, std::max<int64_t>(s.h.xp_size, 1) * el, "Xp");
-      need(r->T2, s.h.u2_size * el, "T2");
-      // x -> row-padded split copy (pads zero), T2 pads zero for R3's padded K
-      CK(cudaMemsetAsync(r->Xp.p, 0, s.h.xp_size * el, st));
-      {
-        Bases bx{};
-        bx.p[S_X] = r->A[j].p;
-        bx.p[S_Y] = r->Xp.p; bx.lo[S_Y] = s.h.xp_size;
-        CK(launch_split_copy(s.xp.d, bx, r->nsplit, st));
-      }
-      CK(cudaMemsetAsync(r->T2.p, 0, s.h.u2_size * el, st));
-      count(3);
-      b.p[S_AUX] = r->Xp.p; b.lo[S_AUX] = s.h.xp_size;
+      int64_t n = s.h.lay.size;
+      split(dptr(r->A[j]), n, r->Xn.p);
+      b.p[S_AUX] = r->Xn.p; b.lo[S_AUX] = n;
       b.p[S_R] = r->Rsp[j + 1].p; b.lo[S_R] = r->Rpsize[j + 1];
       b.lo[S_T2] = s.h.u2_size;
       gemm(s.r1, b, true, 1);
@@ -1965,7 +1950,7 @@ void free_rho(tt_rho* r) {
   for (auto* v : {&r->sp, &r->sp64})
     for (auto& s : *v) {
       release(c, s.s1); release(c, s.s2); release(c, s.s3); release(c, s.s3l); release(c, s.r1); release(c, s.r2);
-      release(c, s.r3); release(c, s.xs); release(c, s.xp);
+      release(c, s.r3); release(c, s.xs);
     }
   for (auto& e : r->esplit) release(c, e);
   for (auto& s : r->bp) { release(c, s.b1); release(c, s.b2); release(c, s.xs); release(c, s.ts); }
@@ -1978,7 +1963,7 @@ void free_rho(tt_rho* r) {
   for (auto& g : r->absl) release(c, g);
   for (auto& g : r->absr) release(c, g);
   for (auto& m : r->meas) { release(c, m.t); release(c, m.el); dfree(c, m.items); }
-  for (DBuf* b : {&r->Qk, &r->W, &r->Xs, &r->Xn, &r->Xp, &r->T1, &r->T2, &r->Sb, &r->ws, &r->partial, &r->ks, &r->rs, &r->tmp, &r->obs, &r->el0, &r->el1, &r->tcerr, &r->qrfb})
+  for (DBuf* b : {&r->Qk, &r->W, &r->Xs, &r->Xn, &r->T1, &r->T2, &r->Sb, &r->ws, &r->partial, &r->ks, &r->rs, &r->tmp, &r->obs, &r->el0, &r->el1, &r->tcerr, &r->qrfb})
     dfree(c, *b);
 }
 

@@ -94,7 +94,6 @@ struct SiteDev {
   DevGemmBuf s1, s3, s3l, r1, r3;
   DevGatherBuf s2, r2;
   DevCopyBuf xs;  // split-bf16 mode: x -> transposed padded copy (S1's B operand)
-  DevCopyBuf xp;  // split-bf16 mode: x -> row-padded copy (R1 / R3 A operand)
 };
 struct BondDev {
   bool valid = false;
@@ -148,7 +147,7 @@ struct tt_rho {
   std::vector<tt::DevGemmBuf> absl, absr;
   std::vector<char> absl_ok, absr_ok;
   std::vector<tt::MeasDev> meas;
-  tt::DBuf Qk, W, Xs, Xn, Xp, T1, T2, Sb, ws, partial, ks, rs, tmp, obs, el0, el1, tcerr, qrfb;
+  tt::DBuf Qk, W, Xs, Xn, T1, T2, Sb, ws, partial, ks, rs, tmp, obs, el0, el1, tcerr, qrfb;
   int64_t ldq = 0;
   tt_stats stats{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -166,20 +166,7 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
   }
   P.lenv_size = ER.size;
 
-  // ---- R1 (mixed: A = x with every (a_l, s) row padded to 8 elements and
-  // zero pads, a K-major operand for the tensor-core kernel; xpad copies it)
-  std::vector<int64_t> xpoff(S.blk.size(), 0);
-  if (mixed) {
-    int64_t xp = 0;
-    for (size_t bi = 0; bi < S.blk.size(); ++bi) {
-      const SiteBlock& b = S.blk[bi];
-      xpoff[bi] = xp;
-      const int rows = b.dl * b.m, ldp = pad8i(b.dr);
-      P.xpad.items.push_back(CItem{mkref(S_X, b.off), mkref(S_Y, xp), b.dr, 1, ldp, 1, rows, b.dr});
-      xp += (int64_t)rows * ldp;
-    }
-    P.xp_size = pad8l(xp);
-  }
+  // ---- R1
   std::vector<int64_t> u1off(S.blk.size(), -1), u1ld(S.blk.size(), 0);
   cur = 0;
   for (size_t bi = 0; bi < S.blk.size(); ++bi) {
@@ -190,8 +177,7 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
     u1off[bi] = cur;
     u1ld[bi] = N;
     P.r1.add_group((int)M, (int)N, mkref(S_T1, cur), (int)N, t1flag);
-    if (mixed) P.r1.add_seg(mkref(S_AUX, xpoff[bi]), pad8i(b.dr), 0, mkref(S_R, ERo.off[b.r]), ERo.ld[b.r], 1, b.dr);
-    else P.r1.add_seg(mkref(S_X, b.off), b.dr, 0, mkref(S_R, ERo.off[b.r]), ERo.ld[b.r], 1, b.dr);
+    P.r1.add_seg(mkref(mixed ? S_AUX : S_X, b.off), b.dr, 0, mkref(S_R, ERo.off[b.r]), ERo.ld[b.r], 1, b.dr);
     cur += M * N;
   }
   P.u1_size = cur;
@@ -216,7 +202,7 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
       int bi = S.block_of(a, p);
       if (bi < 0) continue;
       colseg[(size_t)a * S.npq + p] = cols;
-      cols += (int64_t)S.blk[bi].m * wpad(S.blk[bi].dr);  // mixed: (s, a_r) with a_r padded
+      cols += (int64_t)S.blk[bi].m * S.blk[bi].dr;
     }
     u2off[a] = cur;
     u2rows[a] = rows;
@@ -238,7 +224,7 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
         for (int so = 0; so < ob.m; ++so) {
           const int sig = ls.pairs[p][so].first, sgp = ls.pairs[p][so].second;
           GItem it;
-          it.dst = mkref(S_T2, u2off[a] + row0 * u2cols[a] + colseg[(size_t)a * S.npq + p] + (int64_t)so * wpad(ob.dr));
+          it.dst = mkref(S_T2, u2off[a] + row0 * u2cols[a] + colseg[(size_t)a * S.npq + p] + (int64_t)so * ob.dr);
           it.dst_rs = u2cols[a];
           it.rows = BL.dim[lb];
           it.cols = ob.dr;
@@ -280,12 +266,9 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
         int obi = S.block_of(a, p);
         if (obi < 0) continue;
         const SiteBlock& ob = S.blk[obi];
-        // mixed: K runs over the padded (s, a_r) positions; x's pads are zero
-        // and T2's are cleared before the R2 gather
-        const int K = ob.m * wpad(ob.dr);
-        P.r3.add_seg(mkref(mixed ? S_AUX : S_X, mixed ? xpoff[obi] : ob.off), K, 0,
+        int K = ob.m * ob.dr;
+        P.r3.add_seg(mkref(mixed ? S_AUX : S_X, ob.off), K, 0,
                      mkref(S_T2, u2off[a] + row0 * u2cols[a] + colseg[(size_t)a * S.npq + p]), (int)u2cols[a], 1, K);
-        if (mixed) P.r3.flops -= 2.0 * BL.dim[a] * (double)BL.dim[lb] * ob.m * (wpad(ob.dr) - ob.dr);
       }
     }
   P.renv_size = EL.size;

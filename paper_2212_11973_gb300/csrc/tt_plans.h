@@ -14,10 +14,6 @@ struct SitePlanHost {
   // with rows padded to 8 elements (K-major B operand); xsplit copies x there.
   CopyPlan xsplit;
   int64_t xt_size = 0;
-  // split-bf16 mode: R1 and R3 read x with (a_l, s) rows padded to 8 (xpad
-  // copies it; the pads must be zero)
-  CopyPlan xpad;
-  int64_t xp_size = 0;
 };
 // FP64 environment (natural layout) -> split-bf16 copy with rows padded to 8.
 CopyPlan build_env_split(const Bond& B, const std::vector<Q>& chan);
