@@ -35,6 +35,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM traffic per gemm_tc_kernel launch, ncu capture of profile_heff at D = 1024
+# (profiles/gemm_tc_kernel_heff_apply_D1024.md): (16.3 + 30.6 + 150.7 + 5.7) MB / 2
+TC_TRAFFIC_BYTES_PER_LAUNCH = 101.7e6
+
 METRIC = "TDVP s per beta-step & H_eff TFLOP/s at D=1024; mixed vs FP64 at 1e-6 rel err"
 UNIT = "s/beta-step"
 
@@ -362,7 +366,10 @@ def main():
                 "frac": (heff_tflops / peak) if heff_tflops else None,
                 "flops_per_launch": flops / max(heff_n, 1), "avg_launch_ms": heff_ms / max(heff_n, 1),
                 "executed_over_algorithmic": 6 if prec == 2 else (3 if prec == 1 else 1),
-                "peak_note": peak_note, "traffic": None}
+                "peak_note": peak_note, "traffic": TC_TRAFFIC_BYTES_PER_LAUNCH,
+                "traffic_note": "mean DRAM bytes (read + write) per gemm_tc_kernel launch (S1 and S3) from the "
+                                "ncu capture of one D=1024 apply on Gaussian sector tables "
+                                "(profiles/gemm_tc_kernel_heff_apply_D1024.md); not rescaled to this state"}
     cpu = None
     if not args.no_cpu_baseline:
         Ds = 512

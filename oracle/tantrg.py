@@ -7,7 +7,7 @@ transformation"): site tensors A[j] of shape (D_l, 4, 4, D_r) indexed
 [a_l, sigma, sigma', a_r]; sigma is acted on by H, sigma' is a spectator
 because the flow is generated by H (x) I.  rho_h = exp(logscale) * MPS.
 
-Readings taken where the paper is silent (also listed in the design doc):
+Readings taken where the paper is silent:
 * rho_h(beta) = rho_paper(beta/2) = exp(-beta H/2) (bilayer trick), so
   Z = <<rho_h|rho_h>> and E = <<rho_h|H x I|rho_h>> / Z.
 * One beta-step of size dtau = a left-to-right plus a right-to-left half
