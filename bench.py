@@ -152,6 +152,26 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(t: float) -> float:
+    """Largest value of t over the ranks of the default process group (the
+    slowest replica sets the whole-job time); t itself without a group.  The
+    reduction tensor lives on the GPU for NCCL and on the host for gloo."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    x = torch.tensor([t], dtype=torch.float64, device=dev)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def whole_job_seconds_per_step(t_max: float, steps: int, world: int) -> float:
+    """Replicas: every rank evolves its own copy, so in t_max the job advances
+    `world` beta-steps per timed step; seconds per beta-step of the job."""
+    return t_max / (steps * world)
+
+
 def run_batch(args):
     """64 independent 2x8 ladders (drawn U, mu; D cycling 64/96/128), split-BF16
     x6, all stepped by one tt_batch_step per beta-step.  Replicas for N > 1:
@@ -196,11 +216,7 @@ def run_batch(args):
             ev1.record(stream)
             torch.cuda.synchronize()
         launches = sum(b.stats(i)["launches"] for i in range(b.n))
-        t_dev = ev0.elapsed_time(ev1) / 1e3
-        if world > 1:
-            tmax = torch.tensor([t_dev], device="cuda")
-            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-            t_dev = float(tmax.item())
+        t_dev = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
         per_step = t_dev / args.steps
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -310,12 +326,7 @@ def main():
         barrier()
         t_dev = ev0.elapsed_time(ev1) / 1e3
         rho.set_profiling(False)
-        t_max = t_dev
-        if world > 1:
-            tmax = torch.tensor([t_dev], device="cuda")
-            dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-            t_max = float(tmax.item())
-        per_step = t_max / (args.steps * world)
+        per_step = whole_job_seconds_per_step(max_over_ranks(t_dev), args.steps, world)
 
         # ---- end to end through the public API (host wall clock) ----
         barrier()
