@@ -36,8 +36,9 @@ class Workload:
         return self.Lx * self.Wy
 
 
-# Chemical potential giving about 1/8 hole doping at U = 8 in the particle-hole
-# symmetric form (n = 7/8).  Provisional value until the bisection at D = 128.
+# Chemical potential for about 1/8 hole doping at U = 8 in the particle-hole
+# symmetric form (n = 7/8 at beta = 10).  Provisional: the FP64 D = 128 CL4x8
+# bisection bracketed it in [-3.5, -1.52] (n = 0.632 and 0.99995 there).
 MU_EIGHTH_DOPING = -2.0
 
 CLUSTER_2x2 = Workload("2x2 open cluster U=4 mu=0 D=64", 2, 2, False, 1.0, 4.0, 0.0, 1, 64, 0.01, 0.05, 4.0)
