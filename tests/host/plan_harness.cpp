@@ -1,0 +1,267 @@
+// CPU executor of the library's host-built plans, for the CPU test suite.
+//
+// Builds the Hubbard MPO automaton and the block plans with the library's own
+// host code (tt_model.cpp, tt_plans.cpp) and executes the GEMM, gather and
+// copy records in plain FP64 loops with every access bounds-checked, so the
+// index arithmetic of the plans (FP64 layouts and the padded / transposed
+// split-BF16 layouts, the latter emulated with one FP64 level) can be checked
+// against dense contractions without a GPU.  Test infrastructure only.
+#include <cstdint>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "tt_core.h"
+#include "tt_plans.h"
+
+using namespace tt;
+
+namespace {
+
+struct Slots {
+  double* p[8] = {nullptr};
+  int64_t n[8] = {0};
+  double& at(Ref r, int64_t i) {
+    const int s = (int)(r >> 56);
+    const int64_t o = (int64_t)(r & 0x00FFFFFFFFFFFFFFull) + i;
+    if (s < 0 || s > 7 || !p[s] || o < 0 || o >= n[s])
+      throw std::runtime_error("plan access out of bounds: slot " + std::to_string(s) + " index " +
+                               std::to_string(o) + " size " + std::to_string(s >= 0 && s < 8 ? n[s] : -1));
+    return p[s][o];
+  }
+};
+
+void run_gemm(const GemmPlan& P, Slots& S) {
+  for (const GGroup& g : P.groups)
+    for (int m = 0; m < g.M; ++m)
+      for (int n = 0; n < g.N; ++n) {
+        double acc = 0.0;
+        for (int si = g.seg0; si < g.seg1; ++si) {
+          const GSeg& sg = P.segs[si];
+          for (int k = 0; k < sg.K; ++k) {
+            const double a = S.at(sg.A, sg.tA ? (int64_t)k * sg.lda + m : (int64_t)m * sg.lda + k);
+            const double b = S.at(sg.B, sg.tB ? (int64_t)n * sg.ldb + k : (int64_t)k * sg.ldb + n);
+            acc += a * b;
+          }
+        }
+        double& c = S.at(g.C, (int64_t)m * g.ldc + n);
+        c = (g.flags & 1) ? c + acc : acc;
+      }
+}
+
+void run_gather(const GatherPlan& P, Slots& S) {
+  for (const GItem& it : P.items)
+    for (int r = 0; r < it.rows; ++r)
+      for (int c = 0; c < it.cols; ++c) {
+        double acc = 0.0;
+        for (int k = it.c0; k < it.c1; ++k) {
+          const GContrib& cb = P.contribs[k];
+          acc += cb.coef * S.at(cb.src, (int64_t)r * cb.src_rs + c);
+        }
+        S.at(it.dst, (int64_t)r * it.dst_rs + c) = acc;
+      }
+}
+
+void run_copy(const CopyPlan& P, Slots& S) {
+  for (const CItem& it : P.items)
+    for (int r = 0; r < it.rows; ++r)
+      for (int c = 0; c < it.cols; ++c)
+        S.at(it.dst, (int64_t)r * it.dst_rs + (int64_t)c * it.dst_cs) =
+            S.at(it.src, (int64_t)r * it.src_rs + (int64_t)c * it.src_cs);
+}
+
+Mpo model(const int* geom, const double* par) {
+  ModelSpec m{geom[0], geom[1], geom[2], par[0], par[1], par[2], geom[3]};
+  return build_hubbard_mpo(m);
+}
+
+Bond bond_from(const int* qn, const int* qs, const int* qd, int ns) {
+  Bond b;
+  for (int i = 0; i < ns; ++i) {
+    b.q.push_back(Q{qn[i], qs[i]});
+    b.dim.push_back(qd[i]);
+  }
+  return b;
+}
+
+std::string g_err;
+
+template <class F>
+int guarded(F&& f) {
+  try {
+    f();
+    return 0;
+  } catch (const std::exception& e) {
+    g_err = e.what();
+    return 1;
+  }
+}
+
+// split-bf16 environment copy (rows padded to 8), emulated in FP64
+std::vector<double> pad_env(const Bond& B, const std::vector<Q>& ch, const double* env, int64_t n) {
+  EnvLayout P = make_env_layout(B, ch, true);
+  std::vector<double> out(std::max<int64_t>(P.size, 1), 0.0);
+  Slots S;
+  S.p[S_X] = const_cast<double*>(env); S.n[S_X] = n;
+  S.p[S_Y] = out.data(); S.n[S_Y] = P.size;
+  run_copy(build_env_split(B, ch), S);
+  return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* h_error() { return g_err.c_str(); }
+
+// geom = {Lx, Wy, periodic, form}, par = {t, U, mu}
+int h_mpo_shape(const int* geom, const double* par, int* N, int* chan_dims, int cap) {
+  return guarded([&] {
+    Mpo M = model(geom, par);
+    *N = M.N;
+    if (cap < M.N + 1) throw std::runtime_error("cap");
+    for (int k = 0; k <= M.N; ++k) chan_dims[k] = (int)M.chan[k].size();
+  });
+}
+
+// dense W_j[w, sigma, tau, w'] (row-major, dims chl x 4 x 4 x chr)
+int h_mpo_site_dense(const int* geom, const double* par, int j, double* W) {
+  return guarded([&] {
+    Mpo M = model(geom, par);
+    const int chl = (int)M.chan[j].size(), chr = (int)M.chan[j + 1].size();
+    std::memset(W, 0, sizeof(double) * chl * 16 * chr);
+    for (const MpoTerm& t : M.site[j].terms) W[(((int64_t)t.wl * 4 + t.sig) * 4 + t.tau) * chr + t.wr] += t.v;
+  });
+}
+
+// channel charges of bond k (n, 2Sz)
+int h_mpo_chan(const int* geom, const double* par, int k, int* qn, int* qs, int cap) {
+  return guarded([&] {
+    Mpo M = model(geom, par);
+    if (cap < (int)M.chan[k].size()) throw std::runtime_error("cap");
+    for (size_t w = 0; w < M.chan[k].size(); ++w) {
+      qn[w] = M.chan[k][w].n;
+      qs[w] = M.chan[k][w].s;
+    }
+  });
+}
+
+// start / done channel indices at the two boundary bonds
+int h_mpo_boundary(const int* geom, const double* par, int* start0, int* doneN) {
+  return guarded([&] {
+    Mpo M = model(geom, par);
+    *start0 = M.start_ch[0];
+    *doneN = M.done_ch[M.N];
+  });
+}
+
+// Site plans (H_eff apply, left and right environment updates) executed on
+// the CPU.  op: 0 = H_eff apply (in: L (bond j), R (bond j+1), x; out: y),
+// 1 = left environment update (in: L (bond j), x; out: L (bond j+1)),
+// 2 = right environment update (in: R (bond j+1), x; out: R (bond j)).
+// Sectors of bonds j and j+1 concatenated (nsec_lr = {nl, nr}).
+int h_site_op(const int* geom, const double* par, int j, int op, int mixed, const int* nsec_lr, const int* qn,
+              const int* qs, const int* qd, const double* L, int64_t nL, const double* R, int64_t nR,
+              const double* x, int64_t nx, double* out, int64_t nout) {
+  return guarded([&] {
+    Mpo M = model(geom, par);
+    Bond BL = bond_from(qn, qs, qd, nsec_lr[0]);
+    Bond BR = bond_from(qn + nsec_lr[0], qs + nsec_lr[0], qd + nsec_lr[0], nsec_lr[1]);
+    SitePlanHost P = build_site_plan(BL, BR, M.ls, M.site[j].terms, M.chan[j], M.chan[j + 1], mixed != 0);
+    if (nx != P.lay.size) throw std::runtime_error("x size " + std::to_string(P.lay.size));
+    std::vector<double> T1(std::max<int64_t>(std::max(P.t1_size, P.u1_size), 1)),
+        T2(std::max<int64_t>(std::max(P.t2_size, P.u2_size), 1), 0.0);
+    std::vector<double> Lp, Rp, Xs(std::max<int64_t>(P.xt_size, 1), 0.0);
+    Slots S;
+    S.p[S_T1] = T1.data(); S.n[S_T1] = (int64_t)T1.size();
+    S.p[S_T2] = T2.data(); S.n[S_T2] = (int64_t)T2.size();
+    S.p[S_Y] = out; S.n[S_Y] = nout;
+    if (mixed) {
+      Slots C;
+      C.p[S_X] = const_cast<double*>(x); C.n[S_X] = nx;
+      C.p[S_Y] = Xs.data(); C.n[S_Y] = P.xt_size;
+      run_copy(P.xsplit, C);
+      S.p[S_AUX] = const_cast<double*>(x); S.n[S_AUX] = nx;  // natural split copy of x
+      S.p[S_X] = Xs.data(); S.n[S_X] = P.xt_size;
+    } else {
+      S.p[S_X] = const_cast<double*>(x); S.n[S_X] = nx;
+    }
+    if (op == 0 || op == 1) {
+      if (mixed) {
+        Lp = pad_env(BL, M.chan[j], L, nL);
+        S.p[S_L] = Lp.data(); S.n[S_L] = (int64_t)Lp.size();
+      } else {
+        S.p[S_L] = const_cast<double*>(L); S.n[S_L] = nL;
+      }
+    }
+    if (op == 0 || op == 2) {
+      if (mixed) {
+        Rp = pad_env(BR, M.chan[j + 1], R, nR);
+        S.p[S_R] = Rp.data(); S.n[S_R] = (int64_t)Rp.size();
+      } else {
+        S.p[S_R] = const_cast<double*>(R); S.n[S_R] = nR;
+      }
+    }
+    if (op == 0) {
+      if (nout != P.lay.size) throw std::runtime_error("y size");
+      run_gemm(P.s1, S);
+      run_gather(P.s2, S);
+      run_gemm(P.s3, S);
+    } else if (op == 1) {
+      if (nout != P.lenv_size) throw std::runtime_error("L out size " + std::to_string(P.lenv_size));
+      run_gemm(P.s1, S);
+      run_gather(P.s2, S);
+      run_gemm(P.s3l, S);
+    } else {
+      if (nout != P.renv_size) throw std::runtime_error("R out size " + std::to_string(P.renv_size));
+      run_gemm(P.r1, S);
+      run_gather(P.r2, S);
+      run_gemm(P.r3, S);
+    }
+  });
+}
+
+// Bond H_eff apply y = H^(0) x on bond k (L and R both of bond k).
+int h_bond_op(const int* geom, const double* par, int k, int mixed, int nsec, const int* qn, const int* qs,
+              const int* qd, const double* L, int64_t nL, const double* R, int64_t nR, const double* x, int64_t nx,
+              double* y) {
+  return guarded([&] {
+    Mpo M = model(geom, par);
+    Bond B = bond_from(qn, qs, qd, nsec);
+    BondPlanHost P = build_bond_plan(B, M.chan[k], mixed != 0);
+    if (nx != P.mat.size) throw std::runtime_error("x size " + std::to_string(P.mat.size));
+    std::vector<double> T1(std::max<int64_t>(P.t_size, 1)), Tp(std::max<int64_t>(P.tp_size, 1), 0.0),
+        Xs(std::max<int64_t>(P.xt_size, 1), 0.0), Lp, Rp;
+    Slots S;
+    S.p[S_Y] = y; S.n[S_Y] = nx;
+    S.p[S_T1] = T1.data(); S.n[S_T1] = (int64_t)T1.size();
+    if (mixed) {
+      Slots C;
+      C.p[S_X] = const_cast<double*>(x); C.n[S_X] = nx;
+      C.p[S_Y] = Xs.data(); C.n[S_Y] = P.xt_size;
+      run_copy(P.xsplit, C);
+      Lp = pad_env(B, M.chan[k], L, nL);
+      Rp = pad_env(B, M.chan[k], R, nR);
+      S.p[S_X] = Xs.data(); S.n[S_X] = P.xt_size;
+      S.p[S_L] = Lp.data(); S.n[S_L] = (int64_t)Lp.size();
+      S.p[S_R] = Rp.data(); S.n[S_R] = (int64_t)Rp.size();
+      run_gemm(P.b1, S);
+      Slots C2;
+      C2.p[S_T1] = T1.data(); C2.n[S_T1] = (int64_t)T1.size();
+      C2.p[S_Y] = Tp.data(); C2.n[S_Y] = P.tp_size;
+      run_copy(P.tsplit, C2);
+      S.p[S_T2] = Tp.data(); S.n[S_T2] = P.tp_size;
+      run_gemm(P.b2, S);
+    } else {
+      S.p[S_X] = const_cast<double*>(x); S.n[S_X] = nx;
+      S.p[S_L] = const_cast<double*>(L); S.n[S_L] = nL;
+      S.p[S_R] = const_cast<double*>(R); S.n[S_R] = nR;
+      S.p[S_T2] = T1.data(); S.n[S_T2] = (int64_t)T1.size();
+      run_gemm(P.b1, S);
+      run_gemm(P.b2, S);
+    }
+  });
+}
+
+}  // extern "C"
