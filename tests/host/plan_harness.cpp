@@ -6,6 +6,7 @@
 // index arithmetic of the plans (FP64 layouts and the padded / transposed
 // split-BF16 layouts, the latter emulated with one FP64 level) can be checked
 // against dense contractions without a GPU.  Test infrastructure only.
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <stdexcept>
@@ -261,6 +262,95 @@ int h_bond_op(const int* geom, const double* par, int k, int mixed, int nsec, co
       run_gemm(P.b1, S);
       run_gemm(P.b2, S);
     }
+  });
+}
+
+// Left gauge move of site j by the QR plan and the shifted CholeskyQR3 plan:
+// gather the right-sector group matrices, run the Gram / apply / R-product
+// GEMM plans, a CPU restatement of the device Cholesky step (shift, partial
+// sums, identity check and first-order factor of the last pass), then the
+// scatter of Q into the site layout (q, x's size) and of R (r, s_size
+// elements).  fail[r] = 1 for sectors the device would hand to Householder.
+int h_qr_left(int nl, int nr, const int* qn, const int* qs, const int* qd, const double* x, int64_t nx, double* q,
+              double* r, int64_t nrout, int* fail) {
+  return guarded([&] {
+    LocalSpace ls = hubbard_site_space();
+    Bond BL = bond_from(qn, qs, qd, nl), BR = bond_from(qn + nl, qs + nl, qd + nl, nr);
+    SiteLayout S = make_site_layout(BL, BR, ls);
+    if (nx != S.size) throw std::runtime_error("x size " + std::to_string(S.size));
+    QrPlanHost P = build_qr_left(S, BR);
+    if (nrout != P.s_size) throw std::runtime_error("R size " + std::to_string(P.s_size));
+    CholQrPlan CP = build_cholqr(P.jobs, P.ws_size);
+    std::vector<double> ws(std::max<int64_t>(CP.ws_end, 1), 0.0);
+    Slots Sx;
+    Sx.p[S_X] = const_cast<double*>(x); Sx.n[S_X] = nx;
+    Sx.p[S_Y] = q; Sx.n[S_Y] = nx;
+    Sx.p[S_AUX] = r; Sx.n[S_AUX] = nrout;
+    Sx.p[S_AUX2] = ws.data(); Sx.n[S_AUX2] = (int64_t)ws.size();
+    run_copy(P.gather, Sx);
+    std::vector<int> fl(P.jobs.size(), 0);
+    auto chol = [&](const CholJob& J) {
+      const int n = J.n;
+      if (J.shift == 3) { fl[J.sec] = 1; return; }
+      if (fl[J.sec]) return;
+      double* G = &Sx.at(mkref(S_AUX2, J.g), 0);
+      double* R = &Sx.at(mkref(S_AUX2, J.r), 0);
+      double* Ri = &Sx.at(mkref(S_AUX2, J.ri), 0);
+      const int64_t nn = (int64_t)n * n;
+      Sx.at(mkref(S_AUX2, J.g), (int64_t)J.parts * nn - 1);  // bounds of the partials
+      for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j)
+          for (int p = 1; p < J.parts; ++p) G[i * n + j] += G[p * nn + i * n + j];
+      if (J.shift == 2) {
+        double mx = 0.0;
+        for (int i = 0; i < n; ++i)
+          for (int j = i; j < n; ++j) mx = std::max(mx, std::fabs(G[i * n + j] - (i == j ? 1.0 : 0.0)));
+        if (!(mx <= 1e-3)) { fl[J.sec] = 1; return; }
+        if (n * mx <= 1e-8) {
+          for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+              const double e = G[i * n + j];
+              R[i * n + j] = j < i ? 0.0 : (j == i ? 1.0 + 0.5 * (e - 1.0) : e);
+              Ri[i * n + j] = j < i ? 0.0 : (j == i ? 1.0 - 0.5 * (e - 1.0) : -e);
+            }
+          return;
+        }
+      }
+      if (J.shift == 1) {
+        double tr = 0.0;
+        for (int i = 0; i < n; ++i) tr += G[i * n + i];
+        const double sft = 11.0 * ((double)J.m * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * tr;
+        for (int i = 0; i < n; ++i) G[i * n + i] += sft;
+      }
+      for (int64_t e = 0; e < nn; ++e) R[e] = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double d = G[k * n + k];
+        if (!(d > 0.0)) { fl[J.sec] = 1; return; }
+        const double pv = std::sqrt(d);
+        for (int j = k; j < n; ++j) R[k * n + j] = G[k * n + j] / pv;
+        for (int i = k + 1; i < n; ++i)
+          for (int j = i; j < n; ++j) G[i * n + j] -= R[k * n + i] * R[k * n + j];
+      }
+      for (int j = 0; j < n; ++j) {
+        for (int i = j + 1; i < n; ++i) Ri[i * n + j] = 0.0;
+        Ri[j * n + j] = 1.0 / R[j * n + j];
+        for (int i = j - 1; i >= 0; --i) {
+          double acc = 0.0;
+          for (int qq = i + 1; qq <= j; ++qq) acc += R[i * n + qq] * Ri[qq * n + j];
+          Ri[i * n + j] = -acc / R[i * n + i];
+        }
+      }
+    };
+    for (int p = 0; p < 3; ++p) {
+      run_gemm(CP.gram[p], Sx);
+      for (const CholJob& J : CP.cj[p]) chol(J);
+      run_gemm(CP.app[p], Sx);
+    }
+    run_gemm(CP.tt, Sx);
+    run_gemm(CP.rf, Sx);
+    run_copy(P.scatter, Sx);
+    run_copy(P.rout, Sx);
+    for (size_t i = 0; i < fl.size(); ++i) fail[i] = fl[i];
   });
 }
 

@@ -254,3 +254,49 @@ def test_bond_plan_matches_dense_contraction(h, mixed):
     Ld, Rd, Sd = env_to_dense(L, S, ch), env_to_dense(R, S, ch), bondmat_to_dense(x, S)
     ref = np.tensordot(np.tensordot(Ld, Sd, axes=([2], [0])), Rd, axes=([1, 2], [1, 2]))
     assert np.abs(bondmat_to_dense(y, S) - ref).max() < 1e-11 * max(1.0, np.abs(ref).max())
+
+
+def test_cholqr_gauge_plan_factorises_every_sector(h):
+    """Left gauge move of a site by the library's QR and CholeskyQR3 plans
+    (CPU restatement of the device Cholesky step): for every right sector with
+    at least as many rows as columns, X_r = Q_r R_r with Q_r orthonormal and R_r
+    upper triangular with a positive diagonal, to FP64 rounding; sectors with
+    more columns than rows are flagged for the Householder kernel."""
+    SL = wl.gaussian_sectors(40, 1.0, CHARGES, 21)
+    SR = wl.gaussian_sectors(60, 1.0, CHARGES, 22)
+    blocks, nx = site_blocks(SL, SR)
+    x = np.random.default_rng(5).standard_normal(nx)
+    # ill-conditioned columns (condition up to ~1e11, where unshifted CholeskyQR2
+    # would break down): scale the a_r index of each right sector by 10^-k
+    orr, _ = _offsets(SR)
+    Xd = site_to_dense(x, SL, SR)
+    for i, (_, _, d) in enumerate(SR):
+        Xd[..., orr[i]:orr[i] + d] *= np.logspace(0, -11, d)
+    # back to the block layout
+    for l, r, prs, dl, dr, off in blocks:
+        ol, _ = _offsets(SL)
+        b = np.stack([Xd[ol[l]:ol[l] + dl, s, sp, orr[r]:orr[r] + dr] for s, sp in prs], axis=1)
+        x[off:off + b.size] = b.ravel()
+    qn, qs, qd = _secs_arrays(SL, SR)
+    nrout = sum(d * d for _, _, d in SR)
+    q, rr, fail = np.zeros(nx), np.zeros(nrout), (C.c_int * len(SR))()
+    h.h_qr_left.argtypes = [C.c_int, C.c_int, _PI, _PI, _PI, _PD, C.c_int64, _PD, _PD, C.c_int64, _PI]
+    _chk(h, h.h_qr_left(len(SL), len(SR), qn, qs, qd, _pd(x), nx, _pd(q), _pd(rr), nrout, fail))
+    # group matrix of right sector r: rows (l, p, s, a_l) in block order, cols a_r
+    rpos, checked = 0, 0
+    for ri, (_, _, dr) in enumerate(SR):
+        rows = [(off, dl * len(prs)) for l, r, prs, dl, d2, off in blocks if r == ri]
+        m = sum(n for _, n in rows)
+        R = rr[rpos:rpos + dr * dr].reshape(dr, dr)  # the bond matrix S, row-major
+        rpos += dr * dr
+        if m < dr:
+            assert fail[ri] == 1
+            continue
+        assert fail[ri] == 0
+        Xr = np.concatenate([x[o:o + n * dr].reshape(n, dr) for o, n in rows])
+        Qr = np.concatenate([q[o:o + n * dr].reshape(n, dr) for o, n in rows])
+        assert np.abs(Qr @ R - Xr).max() < 1e-13 * np.abs(Xr).max()
+        assert np.abs(Qr.T @ Qr - np.eye(dr)).max() < 1e-13
+        assert np.abs(np.tril(R, -1)).max() == 0.0 and np.all(np.diag(R) > 0)
+        checked += 1
+    assert checked >= len(SR) - 2
