@@ -136,6 +136,17 @@ int h_mpo_site_dense(const int* geom, const double* par, int j, double* W) {
   });
 }
 
+// dense two-site W12[w, (s1 s2), (t1 t2), w''] (chan j x 16 x 16 x chan j+2)
+int h_mpo_two_site_dense(const int* geom, const double* par, int j, double* W) {
+  return guarded([&] {
+    Mpo M = model(geom, par);
+    const int chl = (int)M.chan[j].size(), chr = (int)M.chan[j + 2].size();
+    std::memset(W, 0, sizeof(double) * chl * 256 * chr);
+    for (const MpoTerm& t : combine_two_sites(M, j, product_space(M.ls, M.ls)).terms)
+      W[(((int64_t)t.wl * 16 + t.sig) * 16 + t.tau) * chr + t.wr] += t.v;
+  });
+}
+
 // channel charges of bond k (n, 2Sz)
 int h_mpo_chan(const int* geom, const double* par, int k, int* qn, int* qs, int cap) {
   return guarded([&] {
@@ -162,14 +173,21 @@ int h_mpo_boundary(const int* geom, const double* par, int* start0, int* doneN) 
 // 1 = left environment update (in: L (bond j), x; out: L (bond j+1)),
 // 2 = right environment update (in: R (bond j+1), x; out: R (bond j)).
 // Sectors of bonds j and j+1 concatenated (nsec_lr = {nl, nr}).
-int h_site_op(const int* geom, const double* par, int j, int op, int mixed, const int* nsec_lr, const int* qn,
-              const int* qs, const int* qd, const double* L, int64_t nL, const double* R, int64_t nR,
+// two != 0: the two-site tensor of sites j, j+1 (growth stage): product
+// local space (d = 16, sigma = 4 sigma_j + sigma_{j+1}), W_j W_{j+1} summed
+// over the middle channel, environments of bonds j and j+2.
+int h_site_op(const int* geom, const double* par, int j, int op, int mixed, int two, const int* nsec_lr,
+              const int* qn, const int* qs, const int* qd, const double* L, int64_t nL, const double* R, int64_t nR,
               const double* x, int64_t nx, double* out, int64_t nout) {
   return guarded([&] {
     Mpo M = model(geom, par);
     Bond BL = bond_from(qn, qs, qd, nsec_lr[0]);
     Bond BR = bond_from(qn + nsec_lr[0], qs + nsec_lr[0], qd + nsec_lr[0], nsec_lr[1]);
-    SitePlanHost P = build_site_plan(BL, BR, M.ls, M.site[j].terms, M.chan[j], M.chan[j + 1], mixed != 0);
+    const LocalSpace ls2 = product_space(M.ls, M.ls);
+    const MpoSite w2 = two ? combine_two_sites(M, j, ls2) : MpoSite();
+    const int jr = two ? j + 2 : j + 1;
+    SitePlanHost P = build_site_plan(BL, BR, two ? ls2 : M.ls, two ? w2.terms : M.site[j].terms, M.chan[j],
+                                     M.chan[jr], mixed != 0);
     if (nx != P.lay.size) throw std::runtime_error("x size " + std::to_string(P.lay.size));
     std::vector<double> T1(std::max<int64_t>(std::max(P.t1_size, P.u1_size), 1)),
         T2(std::max<int64_t>(std::max(P.t2_size, P.u2_size), 1), 0.0);
@@ -198,7 +216,7 @@ int h_site_op(const int* geom, const double* par, int j, int op, int mixed, cons
     }
     if (op == 0 || op == 2) {
       if (mixed) {
-        Rp = pad_env(BR, M.chan[j + 1], R, nR);
+        Rp = pad_env(BR, M.chan[jr], R, nR);
         S.p[S_R] = Rp.data(); S.n[S_R] = (int64_t)Rp.size();
       } else {
         S.p[S_R] = const_cast<double*>(R); S.n[S_R] = nR;

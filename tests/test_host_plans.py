@@ -35,7 +35,7 @@ def h(tmp_path_factory):
     lib = C.CDLL(out)
     lib.h_error.restype = C.c_char_p
     I64 = C.c_int64
-    lib.h_site_op.argtypes = [_PI, _PD, C.c_int, C.c_int, C.c_int, _PI, _PI, _PI, _PI,
+    lib.h_site_op.argtypes = [_PI, _PD, C.c_int, C.c_int, C.c_int, C.c_int, _PI, _PI, _PI, _PI,
                               _PD, I64, _PD, I64, _PD, I64, _PD, I64]
     lib.h_bond_op.argtypes = [_PI, _PD, C.c_int, C.c_int, C.c_int, _PI, _PI, _PI, _PD, I64, _PD, I64, _PD, I64, _PD]
     return lib
@@ -77,13 +77,17 @@ class Model:
 
 # ---- the documented block layouts -> dense arrays ---------------------------
 
-def _pairs():
+LOC_Q2 = [(a[0] + b[0], a[1] + b[1]) for a in LOC_Q for b in LOC_Q]  # sigma = 4 sigma_1 + sigma_2
+
+
+def _pairs(loc=LOC_Q):
+    d = len(loc)
     pq = {}
-    for s in range(4):
-        for sp in range(4):
-            c = (LOC_Q[s][0] - LOC_Q[sp][0], LOC_Q[s][1] - LOC_Q[sp][1])
+    for s in range(d):
+        for sp in range(d):
+            c = (loc[s][0] - loc[sp][0], loc[s][1] - loc[sp][1])
             pq.setdefault(c, []).append((s, sp))
-    return [(c, sorted(v, key=lambda t: 4 * t[0] + t[1])) for c, v in sorted(pq.items())]
+    return [(c, sorted(v, key=lambda t: d * t[0] + t[1])) for c, v in sorted(pq.items())]
 
 
 def _offsets(secs):
@@ -94,22 +98,23 @@ def _offsets(secs):
     return out, o
 
 
-def site_blocks(SL, SR):
+def site_blocks(SL, SR, loc=LOC_Q):
     blocks, off = [], 0
     for r, (rn, rs, dr) in enumerate(SR):
         for l, (ln, ls_, dl) in enumerate(SL):
-            for p, (c, prs) in enumerate(_pairs()):
+            for p, (c, prs) in enumerate(_pairs(loc)):
                 if (ln + c[0], ls_ + c[1]) == (rn, rs):
                     blocks.append((l, r, prs, dl, dr, off))
                     off += dl * len(prs) * dr
     return blocks, off
 
 
-def site_to_dense(v, SL, SR):
+def site_to_dense(v, SL, SR, loc=LOC_Q):
     ol, DL = _offsets(SL)
     orr, DR = _offsets(SR)
-    X = np.zeros((DL, 4, 4, DR))
-    blocks, n = site_blocks(SL, SR)
+    d = len(loc)
+    X = np.zeros((DL, d, d, DR))
+    blocks, n = site_blocks(SL, SR, loc)
     assert n == v.size
     for l, r, prs, dl, dr, off in blocks:
         b = v[off:off + dl * len(prs) * dr].reshape(dl, len(prs), dr)
@@ -213,7 +218,7 @@ def test_site_plans_match_dense_contractions(h, geo, j, D, mixed):
 
     def run(op, nout):
         out = np.zeros(nout)
-        _chk(h, h.h_site_op(m.geom, m.par, j, op, mixed, ns, qn, qs, qd, _pd(L), nL, _pd(R), nR, _pd(x), nx,
+        _chk(h, h.h_site_op(m.geom, m.par, j, op, mixed, 0, ns, qn, qs, qd, _pd(L), nL, _pd(R), nR, _pd(x), nx,
                             _pd(out), nout))
         return out
 
@@ -300,3 +305,35 @@ def test_cholqr_gauge_plan_factorises_every_sector(h):
         assert np.abs(np.tril(R, -1)).max() == 0.0 and np.all(np.diag(R) > 0)
         checked += 1
     assert checked >= len(SR) - 2
+
+
+@pytest.mark.parametrize("mixed", [0, 1])
+def test_two_site_plan_matches_dense_contraction(h, mixed):
+    """Growth stage: W_j W_{j+1} combined over the middle channel equals the
+    product of the single-site W's, and the two-site H_eff plan (product local
+    space, d = 16) equals the dense contraction."""
+    m = Model(h, 3, 3, True, 1.0, 4.0, -0.3, 1)
+    j = 3
+    W1, W2 = m.W(j), m.W(j + 1)
+    W12 = np.zeros((m.chi[j], 16, 16, m.chi[j + 2]))
+    _chk(h, h.h_mpo_two_site_dense(m.geom, m.par, j, _pd(W12)))
+    # W12[w, (s1 s2), (t1 t2), u] = sum_v W_j[w, s1, t1, v] W_{j+1}[v, s2, t2, u]
+    dense12 = np.einsum("wacv,vbdu->wabcdu", W1, W2).reshape(m.chi[j], 16, 16, m.chi[j + 2])
+    assert np.abs(W12 - dense12).max() < 1e-14
+    SL = wl.gaussian_sectors(12, 1.0, CHARGES, 31)
+    SR = wl.gaussian_sectors(14, 1.0, CHARGES, 32)
+    cl, cr = m.chan(j), m.chan(j + 2)
+    _, nx = site_blocks(SL, SR, LOC_Q2)
+    nL, nR = env_size(SL, cl), env_size(SR, cr)
+    rng = np.random.default_rng(17)
+    x, L, R = rng.standard_normal(nx), rng.standard_normal(nL), rng.standard_normal(nR)
+    qn, qs, qd = _secs_arrays(SL, SR)
+    y = np.zeros(nx)
+    _chk(h, h.h_site_op(m.geom, m.par, j, 0, mixed, 1, _ia([len(SL), len(SR)]), qn, qs, qd, _pd(L), nL, _pd(R),
+                        nR, _pd(x), nx, _pd(y), nx))
+    Xd = site_to_dense(x, SL, SR, LOC_Q2)
+    Ld, Rd = env_to_dense(L, SL, cl), env_to_dense(R, SR, cr)
+    T = np.tensordot(Ld, Xd, axes=([2], [0]))
+    T = np.tensordot(T, W12, axes=([1, 2], [0, 2]))
+    refy = np.tensordot(T, Rd, axes=([2, 4], [2, 1])).transpose(0, 2, 1, 3)
+    assert np.abs(site_to_dense(y, SL, SR, LOC_Q2) - refy).max() < 1e-11 * max(1.0, np.abs(refy).max())
