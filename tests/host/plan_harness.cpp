@@ -283,6 +283,30 @@ int h_bond_op(const int* geom, const double* par, int k, int mixed, int nsec, co
   });
 }
 
+// Absorb of the bond matrix into a site (identity sector map, as in the
+// 1-TDVP sweep): side 0: A <- S A (S on bond j, the left bond), side 1:
+// A <- A S (S on bond j+1).  S in the block-diagonal bond layout.
+int h_absorb(int side, int nl, int nr, const int* qn, const int* qs, const int* qd, const double* x, int64_t nx,
+             const double* S, int64_t ns, double* y) {
+  return guarded([&] {
+    LocalSpace ls = hubbard_site_space();
+    Bond BL = bond_from(qn, qs, qd, nl), BR = bond_from(qn + nl, qs + nl, qd + nl, nr);
+    SiteLayout L = make_site_layout(BL, BR, ls);
+    if (nx != L.size) throw std::runtime_error("x size");
+    const Bond& B = side == 0 ? BL : BR;
+    BondMatLayout bm = make_bondmat_layout(B);
+    if (ns != bm.size) throw std::runtime_error("S size");
+    std::vector<int> ident(B.nsec());
+    for (int i = 0; i < B.nsec(); ++i) ident[i] = i;
+    GemmPlan G = side == 0 ? build_absorb_left(L, L, B, B, bm.off, ident) : build_absorb_right(L, L, B, B, bm.off, ident);
+    Slots Sl;
+    Sl.p[S_X] = const_cast<double*>(x); Sl.n[S_X] = nx;
+    Sl.p[S_AUX] = const_cast<double*>(S); Sl.n[S_AUX] = ns;
+    Sl.p[S_Y] = y; Sl.n[S_Y] = nx;
+    run_gemm(G, Sl);
+  });
+}
+
 // Left gauge move of site j by the QR plan and the shifted CholeskyQR3 plan:
 // gather the right-sector group matrices, run the Gram / apply / R-product
 // GEMM plans, a CPU restatement of the device Cholesky step (shift, partial

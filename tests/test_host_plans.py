@@ -337,3 +337,22 @@ def test_two_site_plan_matches_dense_contraction(h, mixed):
     T = np.tensordot(T, W12, axes=([1, 2], [0, 2]))
     refy = np.tensordot(T, Rd, axes=([2, 4], [2, 1])).transpose(0, 2, 1, 3)
     assert np.abs(site_to_dense(y, SL, SR, LOC_Q2) - refy).max() < 1e-11 * max(1.0, np.abs(refy).max())
+
+
+@pytest.mark.parametrize("side", [0, 1])
+def test_absorb_plans_match_dense_products(h, side):
+    """A <- S A (left bond) and A <- A S (right bond) through the absorb plans."""
+    SL = wl.gaussian_sectors(25, 1.0, CHARGES, 41)
+    SR = wl.gaussian_sectors(28, 1.0, CHARGES, 42)
+    _, nx = site_blocks(SL, SR)
+    B = SL if side == 0 else SR
+    ns = sum(d * d for _, _, d in B)
+    rng = np.random.default_rng(9)
+    x, S = rng.standard_normal(nx), rng.standard_normal(ns)
+    qn, qs, qd = _secs_arrays(SL, SR)
+    y = np.zeros(nx)
+    h.h_absorb.argtypes = [C.c_int, C.c_int, C.c_int, _PI, _PI, _PI, _PD, C.c_int64, _PD, C.c_int64, _PD]
+    _chk(h, h.h_absorb(side, len(SL), len(SR), qn, qs, qd, _pd(x), nx, _pd(S), ns, _pd(y)))
+    Xd, Sd = site_to_dense(x, SL, SR), bondmat_to_dense(S, B)
+    ref = np.tensordot(Sd, Xd, axes=([1], [0])) if side == 0 else np.tensordot(Xd, Sd, axes=([3], [0]))
+    assert np.abs(site_to_dense(y, SL, SR) - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
