@@ -5,11 +5,12 @@
 // tile (128 rows x 64 K) and of the B tile (128 rows x 64 K, K-major) into
 // 128B-swizzled shared memory, one elected thread issues tcgen05.mma
 // (kind::f16, bf16 x bf16 -> f32, M = 128, N = 128, K = 16) for the level
-// products l_A + l_B < NS into a TMEM accumulator, and every FOLD chunks all
-// 128 threads read the accumulator back (tcgen05.ld) and add it into a
-// two-float (hi, lo) sum kept in TMEM (TwoSum, Knuth TAOCP 4.2.2), so the FP32
-// accumulation error does not grow with K.  The epilogue writes hi + lo as
-// FP32 or FP64.  Two shared-memory stages overlap the TMA of chunk c+1 with the
+// products l_A + l_B < NS, the leading product into one TMEM accumulator and
+// the smaller ones into a second; every FOLD chunks all 128 threads read both
+// back (tcgen05.ld) and add them into a two-float (hi, lo) sum kept in TMEM
+// (TwoSum, Knuth TAOCP 4.2.2), so the FP32 accumulation error does not grow
+// with K.  The epilogue stages hi + lo through shared memory and writes FP32
+// or FP64 rows coalesced.  Two shared-memory stages overlap the TMA of chunk c+1 with the
 // MMAs of chunk c.  Every mbarrier wait is bounded: on expiry the CTA records
 // an error code, drains its own copies in flight, frees its TMEM and returns.
 //
