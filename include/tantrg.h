@@ -177,8 +177,15 @@ tt_status tt_rho_grow(tt_rho* rho, const tt_mpo* mpo, double dtau, double beta_m
  * without a two-site sweep at that D.  Canonical centre must be on site 0. */
 tt_status tt_rho_pad(tt_rho* rho, const tt_mpo* mpo, int D_target);
 
-/* n_steps 1-TDVP beta-steps of size dtau.  Asynchronous on the ctx stream;
- * the block structure is fixed during the call. */
+/* n_steps 1-TDVP beta-steps of size dtau (main text, linear stage; one
+ * beta-step = an L->R and an R->L half sweep, tau = dtau/4 each, Supplement
+ * "Procedure of 1-TDVP").  Asynchronous on the ctx stream; the block structure
+ * is fixed during the call.  On a non-default stream the first call runs one
+ * step with ordinary launches (building plans and buffers) and captures the
+ * next as a CUDA graph; later steps replay it (re-captured after a change of
+ * dtau, of the profiling mode or of any device buffer).  Set the environment
+ * variable TT_CUDA_GRAPH=0 to launch every kernel directly; TT_QR=householder
+ * selects the one-CTA Householder QR for every sector. */
 tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps);
 
 /* Observables at the canonical centre (site 0 after a step).  Synchronises the
