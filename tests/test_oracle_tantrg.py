@@ -282,3 +282,23 @@ def test_lnZ_convex_in_beta():
     tt.run(ompo.hubbard_mpo(m), 0.01, 0.05, 0.81, tt.TruncOpts(16), callback=lambda st, _: rec.append(tt.measure(st)))
     lnZ = np.array([r["lnZ"] for r in rec])
     assert np.all(lnZ[2:] - 2 * lnZ[1:-1] + lnZ[:-2] > -1e-9)
+
+
+def test_symmetric_sweep_is_second_order_in_dtau():
+    """Lie-Trotter scaling at fixed D (Supplement, "Splitting method"; Fig. S7's
+    delta F against tau): from one grown state, 1-TDVP to beta = 1 with dtau =
+    0.2 ... 0.025; the free-energy error against dtau = 1/160 falls by ~4 per
+    halving (the L->R + R->L composition is symmetric, so second order)."""
+    import copy
+    m = om.Model(3, 2, False, U=4.0, mu=0.3, form=1)
+    st0 = tt.run(ompo.hubbard_mpo(m), 0.01, 0.05, 0.21, tt.TruncOpts(12), grow_until=0.21)
+    f = {}
+    for dt in (0.2, 0.1, 0.05, 0.025, 0.00625):
+        st = copy.deepcopy(st0)
+        for _ in range(int(round((1.01 - st.beta) / dt))):
+            tt.tdvp1_step(st, dt)
+        assert abs(st.beta - 1.01) < 1e-9
+        f[dt] = tt.measure(st)["free_energy_per_site"]
+    e = [abs(f[dt] - f[0.00625]) for dt in (0.2, 0.1, 0.05, 0.025)]
+    slopes = [math.log2(e[i] / e[i + 1]) for i in range(3)]
+    assert all(1.8 < s < 2.3 for s in slopes), slopes
