@@ -80,8 +80,9 @@ typedef struct {
 /* Hubbard model, Eq. 3.  interaction_form 0: U n_up n_dn (Eq. 3);
  * 1: U (n_up - 1/2)(n_dn - 1/2), the particle-hole symmetric form of the DQMC
  * appendix (mu = 0 is half filling).  Lx >= 1 columns (open), Wy >= 1 rows;
- * bc_y_periodic wraps y when Wy > 2.  tp (next-nearest hopping, Eq. S1) must be
- * 0 in this version.  Lx * Wy <= 512. */
+ * bc_y_periodic wraps y when Wy > 2.  tp: next-nearest (diagonal) hopping of
+ * the t-t' model (Supplement, t-t'-U model), -tp (c+_i c_j + h.c.) on the pairs
+ * (x, y)-(x+1, y+-1); 0 gives Eq. 3.  Lx * Wy <= 512. */
 typedef struct {
   int Lx, Wy, bc_y_periodic;
   double t, tp, U, mu;

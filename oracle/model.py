@@ -29,6 +29,8 @@ class Model:
 
     form 0: H = -t sum (c+c + h.c.) + U sum n_up n_dn - mu sum n          (Eq. 3)
     form 1: H = -t sum (c+c + h.c.) + U sum (n_up-1/2)(n_dn-1/2) - mu sum n
+    tp: next-nearest (diagonal) hopping -t' of the t-t' model (Supplement,
+    t-t'-U model), 0 for Eq. 3.
     """
     Lx: int
     Wy: int
@@ -37,6 +39,7 @@ class Model:
     U: float = 0.0
     mu: float = 0.0
     form: int = 1
+    tp: float = 0.0
 
     @property
     def N(self) -> int:
@@ -70,12 +73,39 @@ def lattice_bonds(m: Model) -> list[tuple[int, int]]:
     return sorted(out)
 
 
+def diagonal_bonds(m: Model) -> list[tuple[int, int]]:
+    """Next-nearest (diagonal) pairs (x, y)-(x+1, y+-1) in 1D order; y wraps
+    under the same rule as the nearest-neighbour bonds (only when Wy > 2)."""
+    out = set()
+    for x in range(m.Lx - 1):
+        for y in range(m.Wy):
+            for dy in (1, -1):
+                yy = y + dy
+                if not 0 <= yy < m.Wy:
+                    if not (m.periodic_y and m.Wy > 2):
+                        continue
+                    yy %= m.Wy
+                i, j = snake_index(x, y, m.Wy), snake_index(x + 1, yy, m.Wy)
+                out.add((min(i, j), max(i, j)))
+    return sorted(out)
+
+
+def hopping_bonds(m: Model) -> dict[tuple[int, int], float]:
+    """Hopping amplitude of every pair (i < j): t on nearest neighbours, t' on
+    the diagonals when t' != 0 (H contains -amp (c+_i c_j + h.c.))."""
+    amp = {b: m.t for b in lattice_bonds(m)}
+    if m.tp != 0.0:
+        for b in diagonal_bonds(m):
+            amp[b] = amp.get(b, 0.0) + m.tp
+    return amp
+
+
 def hopping_matrix(m: Model) -> np.ndarray:
-    """Single-particle matrix of the kinetic term of Eq. 3 (no chemical potential)."""
+    """Single-particle matrix of the kinetic term (no chemical potential)."""
     h = np.zeros((m.N, m.N))
-    for i, j in lattice_bonds(m):
-        h[i, j] -= m.t
-        h[j, i] -= m.t
+    for (i, j), a in hopping_bonds(m).items():
+        h[i, j] -= a
+        h[j, i] -= a
     return h
 
 
@@ -123,10 +153,10 @@ def dense_hamiltonian(m: Model) -> sp.csr_matrix:
     num = [cd[k] @ c[k] for k in range(2 * N)]
     dim = 4 ** N
     H = sp.csr_matrix((dim, dim))
-    for i, j in lattice_bonds(m):
+    for (i, j), amp in hopping_bonds(m).items():
         for s in range(2):
             a, b = 2 * i + s, 2 * j + s
-            H = H - m.t * (cd[a] @ c[b] + cd[b] @ c[a])
+            H = H - amp * (cd[a] @ c[b] + cd[b] @ c[a])
     eye = sp.identity(dim, format="csr")
     for i in range(N):
         nu, nd = num[2 * i], num[2 * i + 1]

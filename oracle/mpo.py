@@ -28,7 +28,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .model import Model, lattice_bonds
+from .model import Model, hopping_bonds
 
 
 def local_operators() -> dict[str, np.ndarray]:
@@ -51,9 +51,9 @@ def local_operators() -> dict[str, np.ndarray]:
 
 
 def max_range(m: Model) -> int:
-    """Largest 1D distance j - i over the lattice bonds (2W-1 for a snake cylinder)."""
-    bonds = lattice_bonds(m)
-    return max((j - i for i, j in bonds), default=1)
+    """Largest 1D distance j - i over the hopping pairs (2W-1 for a snake
+    cylinder with nearest-neighbour hopping)."""
+    return max((j - i for i, j in hopping_bonds(m)), default=1)
 
 
 def hubbard_mpo(m: Model) -> list[np.ndarray]:
@@ -63,7 +63,7 @@ def hubbard_mpo(m: Model) -> list[np.ndarray]:
     R = max_range(m)
     nch = R
     DH = 2 + 4 * nch
-    bonds = set(lattice_bonds(m))
+    bonds = hopping_bonds(m)
     lefts = [op["cd_up"] @ op["F"], op["cd_dn"] @ op["F"], op["F"] @ op["c_up"], op["F"] @ op["c_dn"]]
     rights = [op["c_up"], op["c_dn"], op["cd_up"], op["cd_dn"]]
     if m.form == 0:
@@ -88,7 +88,7 @@ def hubbard_mpo(m: Model) -> list[np.ndarray]:
             for dist in range(1, nch + 1):
                 # the term closes here when the left operator sat at j - dist
                 if (j - dist, j) in bonds:
-                    W[ch(o, dist), :, :, 1] = -m.t * rights[o]
+                    W[ch(o, dist), :, :, 1] = -bonds[(j - dist, j)] * rights[o]
         if j == 0:
             W = W[0:1]
         if j == N - 1:

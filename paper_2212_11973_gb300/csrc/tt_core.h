@@ -123,8 +123,12 @@ struct ModelSpec {
   int Lx, Wy, periodic;
   double t, U, mu;
   int form;
+  double tp = 0.0;  // next-nearest (diagonal) hopping of the t-t' model
 };
 std::vector<std::pair<int, int>> lattice_bonds(const ModelSpec& m);
+// Hopping amplitude of every pair (i < j) in 1D order: t on nearest
+// neighbours, tp on the diagonals (x, y)-(x+1, y+-1) when tp != 0.
+std::map<std::pair<int, int>, double> hopping_bonds(const ModelSpec& m);
 Mpo build_hubbard_mpo(const ModelSpec& m);
 // Two-site MPO (W_j W_{j+1} summed over the middle channel) on the product space.
 MpoSite combine_two_sites(const Mpo& mpo, int j, const LocalSpace& ls2);

@@ -2016,8 +2016,8 @@ tt_status tt_hubbard_mpo_create(tt_ctx* ctx, const tt_model* m, tt_mpo** out) {
     ctx->err = "geometry must satisfy Lx, Wy >= 1, 2 <= Lx*Wy <= 512";
     return TT_ERR_INVALID_ARG;
   }
-  if (m->tp != 0.0) {
-    ctx->err = "next-nearest hopping tp is not supported";
+  if (!std::isfinite(m->tp)) {
+    ctx->err = "next-nearest hopping tp must be finite";
     return TT_ERR_INVALID_ARG;
   }
   if (m->interaction_form != 0 && m->interaction_form != 1) {
@@ -2031,7 +2031,7 @@ tt_status tt_hubbard_mpo_create(tt_ctx* ctx, const tt_model* m, tt_mpo** out) {
   tt_mpo* p = new (std::nothrow) tt_mpo();
   if (!p) return TT_ERR_OOM;
   p->ctx = ctx;
-  p->spec = ModelSpec{m->Lx, m->Wy, m->bc_y_periodic, m->t, m->U, m->mu, m->interaction_form};
+  p->spec = ModelSpec{m->Lx, m->Wy, m->bc_y_periodic, m->t, m->U, m->mu, m->interaction_form, m->tp};
   p->mpo = build_hubbard_mpo(p->spec);
   p->ls2 = product_space(p->mpo.ls, p->mpo.ls);
   *out = p;

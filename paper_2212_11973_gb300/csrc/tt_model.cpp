@@ -152,6 +152,24 @@ std::vector<std::pair<int, int>> lattice_bonds(const ModelSpec& m) {
   return std::vector<std::pair<int, int>>(out.begin(), out.end());
 }
 
+std::map<std::pair<int, int>, double> hopping_bonds(const ModelSpec& m) {
+  std::map<std::pair<int, int>, double> amp;
+  for (auto& b : lattice_bonds(m)) amp[b] += m.t;
+  if (m.tp != 0.0)
+    for (int x = 0; x + 1 < m.Lx; ++x)
+      for (int y = 0; y < m.Wy; ++y)
+        for (int dy : {1, -1}) {
+          int yy = y + dy;
+          if (yy < 0 || yy >= m.Wy) {
+            if (!(m.periodic && m.Wy > 2)) continue;
+            yy = (yy + m.Wy) % m.Wy;
+          }
+          const int i = snake(x, y, m.Wy), j = snake(x + 1, yy, m.Wy);
+          amp[{std::min(i, j), std::max(i, j)}] += m.tp;
+        }
+  return amp;
+}
+
 namespace {
 // 4x4 local operators as dense row-major arrays, basis sigma = n_up + 2 n_dn.
 struct Op4 {
@@ -189,8 +207,9 @@ Mpo build_hubbard_mpo(const ModelSpec& m) {
   M.Wy = m.Wy;
   M.ls = hubbard_site_space();
   const int N = M.N;
-  auto bonds = lattice_bonds(m);
-  std::set<std::pair<int, int>> bset(bonds.begin(), bonds.end());
+  const auto amp = hopping_bonds(m);
+  std::vector<std::pair<int, int>> bonds;
+  for (auto& kv : amp) bonds.push_back(kv.first);
 
   // local operators: c_up = a_up, c_dn = F_up a_dn (up before down in a site)
   Op4 a_up, a_dn;
@@ -268,7 +287,7 @@ Mpo build_hubbard_mpo(const ModelSpec& m) {
         if (i >= j) continue;
         int wl = chan(j, {2, o, i});
         if (wl < 0) continue;
-        if (b.second == j) add(wl, dr, right[o], -m.t);   // the hop (i, j) closes here
+        if (b.second == j) add(wl, dr, right[o], -amp.at(b));  // the hop (i, j) closes here
       }
       // pass-through: a pending channel (o, i) continues with the parity F
       for (auto& kv : cidx[j]) {

@@ -72,8 +72,9 @@ void run_copy(const CopyPlan& P, Slots& S) {
             S.at(it.src, (int64_t)r * it.src_rs + (int64_t)c * it.src_cs);
 }
 
+// geom = {Lx, Wy, periodic, form}, par = {t, U, mu, tp}
 Mpo model(const int* geom, const double* par) {
-  ModelSpec m{geom[0], geom[1], geom[2], par[0], par[1], par[2], geom[3]};
+  ModelSpec m{geom[0], geom[1], geom[2], par[0], par[1], par[2], geom[3], par[3]};
   return build_hubbard_mpo(m);
 }
 
@@ -116,7 +117,6 @@ extern "C" {
 
 const char* h_error() { return g_err.c_str(); }
 
-// geom = {Lx, Wy, periodic, form}, par = {t, U, mu}
 int h_mpo_shape(const int* geom, const double* par, int* N, int* chan_dims, int cap) {
   return guarded([&] {
     Mpo M = model(geom, par);

@@ -54,10 +54,10 @@ def _chk(lib, rc):
 
 
 class Model:
-    def __init__(self, lib, Lx, Wy, periodic, t, U, mu, form):
+    def __init__(self, lib, Lx, Wy, periodic, t, U, mu, form, tp=0.0):
         self.lib = lib
         self.geom = _ia([Lx, Wy, int(periodic), form])
-        self.par = (C.c_double * 3)(t, U, mu)
+        self.par = (C.c_double * 4)(t, U, mu, tp)
         N = C.c_int()
         dims = _ia([0] * 600)
         _chk(lib, lib.h_mpo_shape(self.geom, self.par, C.byref(N), dims, 600))
@@ -170,12 +170,15 @@ def _secs_arrays(*bonds):
 
 # ---- tests -------------------------------------------------------------------
 
-@pytest.mark.parametrize("geo", [(2, 2, False, 0), (2, 2, False, 1), (3, 1, False, 1), (2, 3, True, 1)])
+@pytest.mark.parametrize("geo", [(2, 2, False, 0, 0.0), (2, 2, False, 1, 0.0), (3, 1, False, 1, 0.0),
+                                 (2, 3, True, 1, 0.0), (2, 2, False, 1, -0.3), (2, 3, True, 0, 0.25),
+                                 (3, 2, False, 1, -0.2)])
 def test_mpo_automaton_equals_second_quantised_H(h, geo):
     """The library's compressed automaton contracts to the oracle's H (Eq. 3 /
-    PH-symmetric form) built from fermionic modes with Jordan-Wigner."""
-    Lx, Wy, per, form = geo
-    m = Model(h, Lx, Wy, per, 1.0, 4.0, 0.3, form)
+    PH-symmetric form, with and without the t' diagonals) built from
+    fermionic modes with Jordan-Wigner."""
+    Lx, Wy, per, form, tp = geo
+    m = Model(h, Lx, Wy, per, 1.0, 4.0, 0.3, form, tp)
     s0, dN = C.c_int(), C.c_int()
     _chk(h, h.h_mpo_boundary(m.geom, m.par, C.byref(s0), C.byref(dN)))
     T = np.zeros((1, 1, m.chi[0]))
@@ -183,7 +186,7 @@ def test_mpo_automaton_equals_second_quantised_H(h, geo):
     for j in range(m.N):
         T = np.einsum("abw,wstv->asbtv", T, m.W(j)).reshape(T.shape[0] * 4, T.shape[1] * 4, m.chi[j + 1])
     H = T[:, :, dN.value]
-    ref = om.dense_hamiltonian(om.Model(Lx, Wy, per, 1.0, 4.0, 0.3, form)).toarray()
+    ref = om.dense_hamiltonian(om.Model(Lx, Wy, per, 1.0, 4.0, 0.3, form, tp)).toarray()
     assert np.abs(H - ref).max() < 1e-12
 
 
@@ -198,13 +201,14 @@ def _random_bonds(D, seed):
 
 # sector dimensions 1..9 (not multiples of 8: the split-BF16 layouts pad)
 CASES = [((4, 2, False, 1), 3, 30), ((3, 3, True, 1), 4, 40)]
+TP = {(4, 2, False, 1): 0.0, (3, 3, True, 1): -0.25}  # the cylinder case has t' diagonals
 
 
 @pytest.mark.parametrize("geo,j,D", CASES)
 @pytest.mark.parametrize("mixed", [0, 1])
 def test_site_plans_match_dense_contractions(h, geo, j, D, mixed):
     Lx, Wy, per, form = geo
-    m = Model(h, Lx, Wy, per, 1.0, 4.0, -0.3, form)
+    m = Model(h, Lx, Wy, per, 1.0, 4.0, -0.3, form, TP[geo])
     SL, SR = _random_bonds(D, 7 + j)
     cl, cr = m.chan(j), m.chan(j + 1)
     W = m.W(j)

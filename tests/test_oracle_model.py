@@ -20,6 +20,8 @@ GEOMS = [
     om.Model(3, 2, False, U=2.0, mu=-0.5, form=1),
     om.Model(1, 3, True, U=1.0, mu=0.1, form=0),
     om.Model(2, 3, True, U=3.0, mu=0.2, form=1),
+    om.Model(3, 2, False, U=2.0, mu=-0.5, form=1, tp=-0.3),   # t-t' model
+    om.Model(2, 3, True, U=3.0, mu=0.2, form=0, tp=0.25),
 ]
 
 
@@ -92,10 +94,12 @@ def test_planted_wrong_string_operator_is_caught(monkeypatch):
     assert np.abs(H - Hm).max() > 0.5
 
 
-@pytest.mark.parametrize("geom", [(2, 2, False), (4, 2, False), (2, 3, True)])
-def test_ed_matches_free_fermion_closed_form(geom):
-    """U = 0: ED thermodynamics equal the single-particle closed forms."""
-    m = om.Model(*geom, U=0.0, mu=0.37, form=1)
+@pytest.mark.parametrize("geom,tp", [((2, 2, False), 0.0), ((4, 2, False), 0.0), ((2, 3, True), 0.0),
+                                     ((3, 2, False), -0.3)])
+def test_ed_matches_free_fermion_closed_form(geom, tp):
+    """U = 0: ED thermodynamics equal the single-particle closed forms (also
+    with the t' diagonals, whose single-particle matrix is built separately)."""
+    m = om.Model(*geom, U=0.0, mu=0.37, form=1, tp=tp)
     betas = [0.1, 1.0, 4.0]
     ed = om.ed_thermo(m, betas)
     ff = om.free_fermion_thermo(m, betas)
@@ -168,3 +172,15 @@ def test_golden_ed_values_reproduce():
     for got, want in zip(rows, data["rows"]):
         for k in ("lnZ", "energy_per_site", "density", "double_occ"):
             assert abs(got[k] - want[k]) <= 1e-12 * max(1.0, abs(want[k]))
+
+
+def test_diagonal_bonds_of_a_cylinder():
+    """t' pairs: 2 per (x, y) column pair on a periodic cylinder of width W > 2
+    (W (Lx - 1) each way), fewer on open edges; none for one column."""
+    assert len(om.diagonal_bonds(om.Model(4, 4, True))) == 2 * 4 * 3
+    assert len(om.diagonal_bonds(om.Model(4, 2, False))) == 2 * 3
+    assert len(om.diagonal_bonds(om.Model(1, 4, True))) == 0
+    m = om.Model(3, 3, True, tp=0.5)
+    h = om.hopping_matrix(m)
+    for i, j in om.diagonal_bonds(m):
+        assert h[i, j] == -0.5 and h[j, i] == -0.5
