@@ -189,3 +189,26 @@ def test_profiled_graph_replay_reports_times(tt):
         c.close()
     assert s["step_ms"] > 0 and s["heff_ms"] > 0 and s["env_ms"] > 0 and s["qr_ms"] > 0
     assert s["heff_ms"] + s["env_ms"] + s["qr_ms"] < s["step_ms"]
+
+
+def test_cluster_2x2_t_prime_fp64_matches_oracle(tt, ctx):
+    """t-t' model (diagonal hopping t' = -0.3) on the 2x2 cluster: GPU FP64
+    against the oracle, growth and 1-TDVP steps."""
+    from oracle import model as om
+    from oracle import mpo as ompo
+    from oracle import tantrg as ot
+    cfg = wl.CLUSTER_2x2
+    tp = -0.3
+    mpo = tt.Mpo(ctx, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form, tp=tp)
+    rho = tt.Rho(ctx, mpo, cfg.beta0, tt.run_opts(cfg.D, cfg.krylov, 0))
+    rho.grow(cfg.dtau, 0.3)
+    rho.step(cfg.dtau, 4)
+    got = rho.measure()
+    rho.close()
+    mpo.close()
+    m = om.Model(cfg.Lx, cfg.Wy, cfg.periodic, cfg.t, cfg.U, cfg.mu, cfg.form, tp)
+    st = ot.run(ompo.hubbard_mpo(m), cfg.beta0, cfg.dtau, got["beta"] - 1e-9, ot.TruncOpts(cfg.D), K=cfg.krylov,
+                grow_until=0.3)
+    want = ot.measure(st)
+    for k in KEYS_FP64:
+        assert _rel(got[k], want[k]) < 1e-10, (k, got[k], want[k])
