@@ -1,17 +1,22 @@
 """Benchmark: seconds per 1-TDVP beta-step and site-H_eff TFLOP/s at D = 1024.
 
 Workload (default): CL6x12 Hubbard cylinder (width 6 periodic, length 12,
-snake order, N = 72), t = 1, U = 8, mu for about 1/8 hole doping (particle-hole
+snake order, N = 72), t = 1, U = 8, mu for 1/8 hole doping (particle-hole
 symmetric form), block-sparse U(1)xU(1) MPO rho_h with D = 1024, dtau = 0.05,
 Krylov K = 8, split-BF16 x6 tensor-core contractions with FP64 Lanczos, QR,
 exponential and log-norm.
 
 Preparation (untimed): rho_h(beta0) = I - beta0 H/2, 2-TDVP growth at
 D_grow = 256, zero-weight padding of every bond to D = 1024, W warm-up
-beta-steps (which populate the padded directions).  Timed: K beta-steps
-(each an L->R plus an R->L 1-TDVP half sweep with tau = dtau/4), CUDA events
-on the library stream, barrier + synchronize on both sides, max over ranks.
-The state (> 1 GB) is far larger than L2, so no flush is needed.
+beta-steps (which populate the padded directions); the state is saved as a
+checkpoint.  Timed: K beta-steps (each an L->R plus an R->L 1-TDVP half sweep
+with tau = dtau/4), graph replays without profiling nodes, CUDA events on the
+library stream, barrier + synchronize on both sides, max over ranks.  The
+state (> 1 GB) is far larger than L2, so no flush is needed.  After it: a
+profiled pass (event pairs per launch class and sweep phase) for the roofline
+and the breakdown; the end-to-end loop through the public API; a window of
+beta-steps from the checkpoint in the mixed path and in FP64 (errors of the
+mixed observables and the FP64 path's own seconds per beta-step).
 
 Multi-GPU: replicas only (the sweep is sequential along the chain); each rank
 evolves its own copy and `value` is the whole-job seconds per beta-step.
@@ -19,7 +24,7 @@ evolves its own copy and `value` is the whole-job seconds per beta-step.
 --impl reference times the CPU oracle (dense FP64 NumPy) on a bounded sample
 of the same workload: one dense site H_eff apply at D = 512 with the oracle's
 MPO, scaled by (1024/512)^3 and by the 2N(K+1) site-apply equivalents of a
-beta-step.
+beta-step.  --workload heff-apply runs single site applies for profilers.
 """
 from __future__ import annotations
 
@@ -34,10 +39,6 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-
-# DRAM traffic per gemm_tc_kernel launch, ncu capture of profile_heff at D = 1024
-# (profiles/gemm_tc_kernel_heff_apply_D1024.md): (16.3 + 30.6 + 150.7 + 5.7) MB / 2
-TC_TRAFFIC_BYTES_PER_LAUNCH = 101.7e6
 
 METRIC = "TDVP s per beta-step & H_eff TFLOP/s at D=1024; mixed vs FP64 at 1e-6 rel err"
 UNIT = "s/beta-step"
@@ -127,8 +128,84 @@ def oracle_sample(D: int = 512, seed: int = 7):
     return time.perf_counter() - t0, DH
 
 
+def oracle_window():
+    """A real oracle 1-TDVP beta-step of the CL6x12 workload at the bond
+    dimensions of the compact initial state (max 26): seconds."""
+    from oracle import model as om
+    from oracle import mpo as ompo
+    from oracle import tantrg as ot
+    from paper_2212_11973_gb300 import workloads as wl
+    cfg = wl.CYL_6x12_D1024
+    m = om.Model(cfg.Lx, cfg.Wy, cfg.periodic, cfg.t, cfg.U, cfg.mu, cfg.form)
+    st = ot.init_state(ompo.hubbard_mpo(m), cfg.beta0)
+    t0 = time.perf_counter()
+    ot.tdvp1_step(st, cfg.dtau, K=cfg.krylov)
+    return time.perf_counter() - t0, max(st.bond_dims())
+
+
+_ONE_CORE_ENV = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                  "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS")}
+
+
+def _blas_threads():
+    """BLAS thread count numpy uses (threadpoolctl when importable, else the
+    thread environment variables, else the core count)."""
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n)
+    except Exception:
+        pass
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count()
+
+
+def cpu_baseline(D_all: int = 512, D_one: int = 256, window: bool = True) -> dict:
+    """The oracle as it stands, on the host cores.
+
+    value: one dense site H_eff apply at D_all (all cores), scaled to the
+    CL6x12 D = 1024 beta-step by (1024/D)^3 and the 2N(K+1) site-apply
+    equivalents of a beta-step: a labelled estimate (the dense oracle cannot
+    run a D = 1024 step).  one_core: the same estimate from a D_one apply in a
+    child process with one BLAS thread.  window: a real oracle 1-TDVP
+    beta-step of the same cylinder at the compact initial state's bond
+    dimensions, all cores."""
+    from paper_2212_11973_gb300 import workloads as wl
+    cfg = wl.CYL_6x12_D1024
+    per_step = 2 * cfg.N * (cfg.krylov + 1)
+    t_all = min(oracle_sample(D_all)[0] for _ in range(2))
+    est = t_all * (cfg.D / D_all) ** 3 * per_step
+    env = dict(os.environ, **_ONE_CORE_ENV)
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(min(bench.oracle_sample({D_one})[0] for _ in range(2)))")
+    one = None
+    try:
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        if p.returncode == 0:
+            one = float(p.stdout.strip().splitlines()[-1]) * (cfg.D / D_one) ** 3 * per_step
+    except Exception:
+        one = None
+    out = {"value": est, "unit": UNIT, "cores": os.cpu_count(), "blas_threads": _blas_threads(), "kind": "oracle",
+           "estimate": True,
+           "sample": f"one dense FP64 site H_eff apply at D={D_all} (oracle MPO of CL6x12, random dense L, R, x), "
+                     f"scaled by (1024/{D_all})^3 x 2N(K+1)={per_step} site-apply equivalents per beta-step",
+           "one_core": {"value": one, "blas_threads": 1,
+                        "sample": f"the same apply at D={D_one} in a child process with one BLAS thread, scaled "
+                                  f"by (1024/{D_one})^3 x {per_step}"}}
+    if window:
+        tw, dmax = oracle_window()
+        out["window"] = {"value": tw, "unit": "s/beta-step",
+                         "sample": f"one real oracle 1-TDVP beta-step of CL6x12 (dtau={cfg.dtau}, K={cfg.krylov}) "
+                                   f"from the compact rho_h(beta0), bond dimensions <= {dmax}, all cores"}
+    return out
+
+
 def reference_arm(args):
-    """The oracle timed on the host cores, per 'step' one bounded sample."""
+    """The oracle timed on the host cores; each 'step' is one bounded sample
+    (a dense D = 512 site apply scaled to the D = 1024 beta-step)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -142,12 +219,14 @@ def reference_arm(args):
     per_step = statistics.mean(ts) * scale
     cores = os.cpu_count()
     sample = (f"one dense FP64 site H_eff apply at D={Ds} (oracle MPO of CL6x12), scaled by "
-              f"(1024/{Ds})^3 x 2N(K+1)={2 * cfg.N * (cfg.krylov + 1)} applies per beta-step")
+              f"(1024/{Ds})^3 x 2N(K+1)={2 * cfg.N * (cfg.krylov + 1)} applies per beta-step (an estimate: "
+              f"the dense oracle cannot run a D=1024 beta-step)")
     line = {"impl": "reference", "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": cfg.name, "N": cfg.N, "D": cfg.D, "dtau": cfg.dtau, "krylov": cfg.krylov},
-            "cpu_baseline": {"value": per_step, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": per_step, "unit": UNIT, "cores": cores, "blas_threads": _blas_threads(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": per_step, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -248,6 +327,39 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def heff_apply(args):
+    """One site H_eff apply at the bench sizes (for profilers): CL6x12 Hubbard
+    MPO at the middle site, Gaussian sector tables of total dimension D on both
+    bonds, seeded normal L, R and x, through tt_heff_apply_host (host arrays;
+    split copies, S1, the W-gather and S3).  Small on the device, no graph and
+    no profiler API, so `ncu -k ... -c ...` can capture single launches."""
+    from paper_2212_11973_gb300 import tantrg as tt
+    from paper_2212_11973_gb300 import workloads as wl
+    cfg = wl.CYL_6x12_D1024
+    D = args.D or cfg.D
+    ctx = tt.Context()
+    mpo = tt.Mpo(ctx, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
+    site = cfg.N // 2
+    SL = wl.gaussian_sectors(D, 1.5, wl.SECTOR_CHARGES, 2024)
+    SR = wl.gaussian_sectors(D, 1.5, wl.SECTOR_CHARGES, 2025)
+    nx, nl, nr = tt.layout_sizes(mpo, site, SL, SR)
+    L, R, x = wl.random_vector(nl, 2026), wl.random_vector(nr, 2027), wl.random_vector(nx, 2028)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        y = tt.heff_apply_host(ctx, mpo, site, args.precision, SL, SR, L, R, x)
+        ts.append(time.perf_counter() - t0)
+    print(json.dumps({"workload": f"site H_eff apply, CL6x12 MPO middle site, Gaussian sectors D={D}",
+                      "precision": args.precision, "x": nx, "L": nl, "R": nr, "host_s_per_apply": ts,
+                      "norm_y": float((y * y).sum()) ** 0.5}), flush=True)
+    mpo.close()
+    ctx.close()
+
+
+def _obs_rel(a, b, keys=("energy_per_site", "double_occ", "density", "free_energy_per_site")):
+    return {k: abs(a[k] - b[k]) / abs(b[k]) for k in keys}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -256,10 +368,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--D", type=int, default=None, help="override the bond dimension (debug)")
     ap.add_argument("--grow-D", type=int, default=256)
-    ap.add_argument("--workload", default="cl6x12", choices=["cl6x12", "cl4x8", "cl4x8-mixed", "batch64"])
+    ap.add_argument("--precision", type=int, default=2, help="heff-apply workload: 0 FP64, 1 x3, 2 x6")
+    ap.add_argument("--workload", default="cl6x12",
+                    choices=["cl6x12", "cl4x8", "cl4x8-mixed", "batch64", "heff-apply"])
+    ap.add_argument("--window", type=int, default=3, help="beta-steps of the mixed-vs-FP64 window")
+    ap.add_argument("--save", default=None, help="write the prepared state (checkpoint) to this path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true",
-                    help="skip the mixed-vs-FP64 beta-step from a shared checkpoint")
+                    help="skip the mixed-vs-FP64 window and the FP64 timing from a shared checkpoint")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -270,6 +386,11 @@ def main():
     if args.workload == "batch64":
         run_batch(args)
         return
+    if args.workload == "heff-apply":
+        heff_apply(args)
+        return
+
+    import tempfile
 
     import torch
     import torch.distributed as dist
@@ -291,6 +412,7 @@ def main():
     D = args.D or cfg.D
     prec = cfg.precision
     stream = torch.cuda.Stream()
+    tmpdir = tempfile.mkdtemp()
     with torch.cuda.stream(stream):
         ctx = tt.Context(stream=stream)
         mpo = tt.Mpo(ctx, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
@@ -300,36 +422,46 @@ def main():
         rho.grow(cfg.dtau, 1.0)
         if gD < D:
             rho.pad(D)
-        # profiling mode (CUDA event pairs per launch class, inside the graph)
-        # is switched on before the warm-up so that the timed steps replay the
-        # graph the warm-up captured
-        rho.set_profiling(True)
         for _ in range(args.warmup):
             rho.step(cfg.dtau, 1)
         torch.cuda.synchronize()
         t_prep = time.perf_counter() - t_prep
         dims = rho.bond_dims()
+        ck0 = os.path.join(tmpdir, "c0.ttck")
+        rho.save(ck0)
+        if args.save:
+            rho.save(args.save)
 
-        # ---- timed region (device) ----
+        # ---- timed region (device): graph replays, no profiling nodes ----
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
         rho.stats()  # reset the accumulators
-        torch.cuda.profiler.start()  # ncu --profile-from-start off captures only this region
         with ClockSampler(local) as clk:
             ev0.record(stream)
             for _ in range(args.steps):
                 rho.step(cfg.dtau, 1)
             ev1.record(stream)
             torch.cuda.synchronize()
-        torch.cuda.profiler.stop()
-        s = rho.stats()  # per-launch event times accumulated over the K steps
-        flops, heff_ms, heff_n = s["heff_flops"], s["heff_ms"], s["heff_launches"]
-        env_ms, env_fl, launches = s["env_ms"], s["env_flops"], s["launches"]
+        s_plain = rho.stats()
         barrier()
         t_dev = ev0.elapsed_time(ev1) / 1e3
-        rho.set_profiling(False)
         per_step = whole_job_seconds_per_step(max_over_ranks(t_dev), args.steps, world)
+
+        # ---- profiled pass (separate): CUDA event pairs around every GEMM /
+        # gather launch and sweep phase, recorded inside a re-captured graph ----
+        rho.set_profiling(True)
+        rho.step(cfg.dtau, 1)  # untimed: captures the profiling graph
+        torch.cuda.synchronize()
+        rho.stats()
+        nprof = min(args.steps, 3)
+        with ClockSampler(local) as clk_prof:
+            rho.step(cfg.dtau, nprof)
+            torch.cuda.synchronize()
+        s = rho.stats()
+        rho.set_profiling(False)
+        flops, heff_ms, heff_n = s["heff_flops"], s["heff_ms"], s["heff_launches"]
+        env_ms, env_fl = s["env_ms"], s["env_flops"]
         rho.step(cfg.dtau, 1)  # untimed: re-captures the graph without profiling events
 
         # ---- end to end through the public API (host wall clock) ----
@@ -342,27 +474,45 @@ def main():
             obs = rho.measure()  # synchronises; device -> host copy of the observables
         e2e = (time.perf_counter() - t0) / (args.steps * world)
         barrier()
+        rho.close()
 
-        # ---- mixed vs FP64: one beta-step of each from the same checkpoint ----
+        # ---- mixed vs FP64 over a window of beta-steps from one checkpoint,
+        # and the FP64 path's own time per beta-step (graph replays) ----
         check = None
         if not args.no_fp64_check and rank == 0:
-            import tempfile
-            with tempfile.TemporaryDirectory() as td:
-                path = os.path.join(td, "rho.ttck")
-                rho.save(path)
-                rho.step(cfg.dtau, 1)
-                om = rho.measure()
-                r64 = tt.Rho.load(ctx, mpo, path, tt.run_opts(D, cfg.krylov, 0))
-                t64 = time.perf_counter()
+            nw = max(args.window, 3)
+            rm = tt.Rho.load(ctx, mpo, ck0, tt.run_opts(D, cfg.krylov, prec))
+            rm.step(cfg.dtau, nw)
+            om = rm.measure()
+            rm.close()
+            r64 = tt.Rho.load(ctx, mpo, ck0, tt.run_opts(D, cfg.krylov, 0))
+            t_unc = time.perf_counter()
+            r64.step(cfg.dtau, 1)  # uncaptured step (plans, buffers) + capture
+            torch.cuda.synchronize()
+            t_unc = time.perf_counter() - t_unc
+            t64 = []
+            for _ in range(nw - 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
                 r64.step(cfg.dtau, 1)
-                o64 = r64.measure()
-                t64 = time.perf_counter() - t64
-                r64.close()
-            check = {"beta": om["beta"], "fp64_s_per_step_incl_plans": t64,
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t64.append(e0.elapsed_time(e1) / 1e3)
+            o64 = r64.measure()
+            r64.close()
+            rel = _obs_rel(om, o64)
+            tol = 1e-6
+            check = {"window_beta_steps": nw, "beta": [om["beta"] - nw * cfg.dtau, om["beta"]],
                      "energy_per_site": [om["energy_per_site"], o64["energy_per_site"]],
+                     "double_occ": [om["double_occ"], o64["double_occ"]],
                      "abs_err_energy_per_site": abs(om["energy_per_site"] - o64["energy_per_site"]),
-                     **{f"rel_err_{k}": abs(om[k] - o64[k]) / abs(o64[k])
-                        for k in ("energy_per_site", "double_occ", "density", "free_energy_per_site")}}
+                     **{f"rel_err_{k}": v for k, v in rel.items()},
+                     "tol": tol,
+                     "pass": bool(rel["energy_per_site"] <= tol and rel["double_occ"] <= tol),
+                     "fp64_s_per_step": statistics.median(t64),
+                     "fp64_s_per_step_all": t64,
+                     "fp64_first_step_s_incl_plans": t_unc,
+                     "fp64_over_mixed": statistics.median(t64) / per_step}
 
     if rank != 0:
         if world > 1:
@@ -381,18 +531,11 @@ def main():
                 "frac": (heff_tflops / peak) if heff_tflops else None,
                 "flops_per_launch": flops / max(heff_n, 1), "avg_launch_ms": heff_ms / max(heff_n, 1),
                 "executed_over_algorithmic": 6 if prec == 2 else (3 if prec == 1 else 1),
-                "peak_note": peak_note, "traffic": TC_TRAFFIC_BYTES_PER_LAUNCH,
-                "traffic_note": "mean DRAM bytes (read + write) per gemm_tc_kernel launch (S1 and S3) from the "
-                                "ncu capture of one D=1024 apply on Gaussian sector tables "
-                                "(profiles/gemm_tc_kernel_heff_apply_D1024.md); not rescaled to this state"}
-    cpu = None
-    if not args.no_cpu_baseline:
-        Ds = 512
-        ts = [oracle_sample(Ds)[0] for _ in range(2)]
-        scale = (cfg.D / Ds) ** 3 * 2 * cfg.N * (cfg.krylov + 1)
-        cpu = {"value": min(ts) * scale, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one dense FP64 site H_eff apply at D={Ds} (oracle MPO of CL6x12), scaled by "
-                         f"(1024/{Ds})^3 x 2N(K+1) site-apply equivalents per beta-step"}
+                "peak_note": peak_note, "traffic": None,
+                "measured_in": f"profiled pass of {nprof} graph-replayed beta-steps after the timed region "
+                               "(event pairs around each launch on the library stream)",
+                "traffic_note": "null: no ncu capture of this state's kernels since they last changed"}
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
     line = {
         "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
@@ -403,14 +546,20 @@ def main():
                    "l2": "state larger than L2 (no flush)"},
         "heff_tflops": heff_tflops, "env_tflops": (env_fl / (env_ms / 1e3) / 1e12) if env_ms > 0 else None,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 56,
-                "includes": "tt_tdvp_step + tt_measure (measurement sweep and observables to host)"},
-        "breakdown_ms_per_step": {k: s[k + "_ms"] / args.steps for k in ("heff", "env", "qr", "bond", "gather")},
-        "phases_ms_per_step": {k: s[k + "_ms"] / args.steps
+                "includes": "tt_tdvp_step + tt_measure (measurement sweep and the 56-byte observables to host)",
+                "copies": "the step's input is the device-resident state and dtau (no host payload); only the "
+                          "observables come back"},
+        "breakdown_ms_per_step": {k: s[k + "_ms"] / nprof for k in ("heff", "env", "qr", "bond", "gather")},
+        "phases_ms_per_step": {k: s[k + "_ms"] / nprof
                                for k in ("site_exp", "bond_exp", "env_update", "absorb", "gauge")},
-        "qr_gauge": {"sectors_per_step": s["qr_sectors"] / args.steps,
-                     "householder_fallbacks_per_step": s["qr_fallbacks"] / args.steps},
+        "profiled_s_per_step": s["step_ms"] / 1e3 / nprof if s.get("step_ms") else None,
+        "qr_gauge": {"sectors_per_step": s["qr_sectors"] / nprof,
+                     "householder_fallbacks_per_step": s["qr_fallbacks"] / nprof},
         "mixed_vs_fp64": check,
-        "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
+        "autotune": {"plans_tcgen05_128x128": s["tuned_tc128"], "plans_tcgen05_persistent_128x64": s["tuned_tcp128x64"],
+                     "plans_mma_sync_64x64": s["tuned_mma64"]},
+        "gpu_launches": s_plain["launches"], "roofline": roofline, "cpu_baseline": cpu,
+        "clocks": clk.summary(), "clocks_profiled_pass": clk_prof.summary(),
         "observables": {k: obs[k] for k in ("beta", "energy_per_site", "density", "double_occ",
                                             "free_energy_per_site")} if obs else None,
     }

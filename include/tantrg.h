@@ -57,11 +57,18 @@ typedef enum {
   TT_PREC_MIXED_BF16X3 = 1,  /* H_eff and environment contractions as split-
                                 BF16 tensor-core products, 2 levels / 3
                                 products (~2^-16 relative) */
-  TT_PREC_MIXED_BF16X6 = 2   /* 3 levels / 6 products (~2^-24 relative), FP32
+  TT_PREC_MIXED_BF16X6 = 2,  /* 3 levels / 6 products (~2^-24 relative), FP32
                                 accumulation folded per K chunk into a two-
                                 float sum.  In both mixed modes the Lanczos
                                 vectors, Krylov exponential, QR, SVD, absorb
                                 step, measurements and log-norm stay FP64 */
+  TT_PREC_SPLIT_EXACT = 3    /* FP64 operands cut per 32-wide K tile into four
+                                fixed-point BF16 digits (per-row / per-column
+                                exponent), tensor-core products summed exactly
+                                in FP32 per tile and folded into a two-float
+                                accumulator (Ozaki scheme): ~2^-32 of the
+                                operands' row/column bounds; FP64 layouts, FP64
+                                W-gather */
 } tt_precision;
 
 typedef struct tt_ctx tt_ctx;
@@ -99,6 +106,15 @@ typedef struct {
   double svd_cut;       /* growth: drop s <= svd_cut * s_max (default 1e-12) */
   double degen_tol;     /* growth: never split s_k, s_k+1 with
                            s_k - s_k+1 <= degen_tol s_k + 1e-14 s_max (1e-10) */
+  int env_precision;    /* environment updates.  0 (default): FP64 in the FP64
+                           mode, the exact-accumulation split (as
+                           TT_PREC_SPLIT_EXACT) in the other modes; 1: native
+                           FP64 GEMMs; -1: the arithmetic of `precision`.
+                           Each update feeds the next along the chain, so its
+                           rounding errors compound over the N sites (FP32-
+                           class split products leave ~1e-5 in the energy at
+                           N = 72); the H_eff and bond applies' errors stay
+                           local to one update */
 } tt_run_opts;
 
 typedef struct {
@@ -137,6 +153,11 @@ typedef struct {
      counted above): site exponentials (Lanczos + H_eff applies), bond
      exponentials, environment updates, absorbs, gauge moves (copies + QR) */
   double site_exp_ms, bond_exp_ms, env_update_ms, absorb_ms, gauge_ms;
+  /* split-BF16 GEMM plans of this state by the kernel the tile autotuner
+     chose (first uncaptured use: every eligible kernel timed, fastest kept):
+     tcgen05 128 x 128 tiles, persistent tcgen05 128 x 64 tiles, mma.sync
+     64 x 64 tiles */
+  long long tuned_tc128, tuned_tcp128x64, tuned_mma64;
 } tt_stats;
 
 /* ---- context ---------------------------------------------------------- */
@@ -147,6 +168,14 @@ tt_status tt_ctx_create(const tt_alloc_cb* alloc, void* cuda_stream, tt_ctx** ou
 void tt_ctx_destroy(tt_ctx* ctx);
 /* Message of the last failed call on this context ("" if none).  Owned by ctx. */
 const char* tt_last_error(const tt_ctx* ctx);
+/* Time budget, in seconds (0..60, default 2), of every bounded device-side wait
+ * of this context's kernels (the tcgen05 GEMM's copy and MMA barriers).  A wait
+ * that runs out makes the kernel record an error, drain its own copies in flight
+ * and return; the next synchronising call on the object (tt_measure, tt_rho_grow,
+ * tt_heff_apply_host) then returns TT_ERR_TIMEOUT and poisons it, while the
+ * context stays usable.  0 means a single non-blocking test per wait.  Takes
+ * effect for the following launches (a captured beta-step is re-captured). */
+tt_status tt_ctx_set_wait_limit(tt_ctx* ctx, double seconds);
 
 /* ---- Hubbard MPO (Eq. 3; built on the host as a finite automaton with
  *      U(1)xU(1) labels on every leg, uploaded to the device) --------------- */
@@ -159,8 +188,15 @@ int tt_mpo_bond_dim(const tt_mpo* mpo, int k);
 /* ---- state ------------------------------------------------------------- */
 
 /* rho_h(beta0) = I - beta0 H / 2 (main text: rho_0 = 1 - tau_0 H from the MPO
- * of H), right-canonicalised by LQ sweeps (canonical centre on site 0).
- * taylor_order must be 1 in this version. */
+ * of H), right-canonicalised by LQ sweeps (canonical centre on site 0), for
+ * taylor_order = 1.  taylor_order = n in 2..8: the series-expansion initial
+ * state sum_{k <= n} (-beta0 H / 2)^k / k! (Supplement, "Error analysis of
+ * tanTRG": SETTN initialisation), built by Horner's rule, each step a local
+ * MPO x super-MPS product plus the identity, compressed by SVD (singular
+ * values <= 1e-14 s_max dropped); the bond dimension before each compression
+ * is (MPO bond) x (current bond) + 1, so high orders suit small systems or
+ * small beta0.  Every order keeps the bond dimensions the compression leaves
+ * (tt_rho_grow then starts from them). */
 tt_status tt_rho_create(tt_ctx* ctx, const tt_mpo* mpo, double beta0, int taylor_order,
                         const tt_run_opts* opts, tt_rho** out);
 void tt_rho_destroy(tt_rho* rho);
@@ -170,6 +206,13 @@ void tt_rho_destroy(tt_rho* rho);
  * reached to *beta_reached (host, may be NULL).  Synchronises the stream. */
 tt_status tt_rho_grow(tt_rho* rho, const tt_mpo* mpo, double dtau, double beta_max,
                       double* beta_reached);
+/* The growth stage on an exponential grid (main text: "we always start with
+ * exponential grids and exploit the two-site update"; Fig. S7(b): beta_n =
+ * 2^(n/m) beta_0): every 2-TDVP beta-step takes beta -> ratio * beta (the last
+ * one clipped to beta_max), 1 < ratio <= 4, with the same stop rule as
+ * tt_rho_grow.  Synchronises the stream. */
+tt_status tt_rho_grow_exp(tt_rho* rho, const tt_mpo* mpo, double ratio, double beta_max,
+                          double* beta_reached);
 
 /* Enlarge every bond to about D_target states (each sector scaled by
  * D_target / D, within what the neighbouring blocks can hold) with zero-weight
@@ -270,6 +313,27 @@ tt_status tt_heff_apply_host(tt_ctx* ctx, const tt_mpo* mpo, int site, int preci
                              const int* nsec_lr, const int* qn, const int* qs, const int* qd,
                              const double* L, const double* R, const double* x, double* y);
 
+/* The same site apply (Supplement, "Lanczos-based exponential method": the
+ * L W A R contraction) with the MPO tensor W given by the caller instead of a
+ * tt_mpo: channels w = 0..nw_l-1 of the left MPO bond with charges
+ * (chl_qn[w], chl_qs[w]), channels of the right MPO bond likewise, and nterms
+ * nonzero entries W[wl][wr] <sig| op |tau> = t_val (host arrays t_wl, t_wr,
+ * t_sig, t_tau in 0..3 of the local basis above, t_val).  Every term must
+ * satisfy c_wr = c_wl + q(sig) - q(tau) (q = (particle number, 2 Sz)), else
+ * TT_ERR_INVALID_ARG.  Sector tables, L, R, x, y and precision as in
+ * tt_heff_apply_host, with the environments' channel index running over these
+ * channels.  tt_layout_sizes_terms gives the element counts of x, L, R. */
+tt_status tt_heff_apply_terms_host(tt_ctx* ctx, int nw_l, const int* chl_qn, const int* chl_qs,
+                                   int nw_r, const int* chr_qn, const int* chr_qs,
+                                   int nterms, const int* t_wl, const int* t_wr, const int* t_sig,
+                                   const int* t_tau, const double* t_val, int precision,
+                                   const int* nsec_lr, const int* qn, const int* qs, const int* qd,
+                                   const double* L, const double* R, const double* x, double* y);
+tt_status tt_layout_sizes_terms(int nw_l, const int* chl_qn, const int* chl_qs, int nw_r,
+                                const int* chr_qn, const int* chr_qs, const int* nsec_lr,
+                                const int* qn, const int* qs, const int* qd,
+                                int64_t* x_size, int64_t* l_size, int64_t* r_size);
+
 /* QR gauge kernel on one matrix (Supplement, "Procedure of 1-TDVP", step 3:
  * A_i = A_i^L S_i by QR): A = Q R for a column-major m x n matrix (ld = m,
  * 1 <= n <= min(m, 2048)), Householder in FP64, sign convention diag(R) >= 0.
@@ -283,9 +347,12 @@ tt_status tt_qr_device(tt_ctx* ctx, const double* A, int m, int n, double* Q, do
  * owned by another framework, a latency-bound path where cudaMalloc could
  * synchronise).  The paper has no counterpart; this is a library service.
  *   Scratch: a fixed 16 MiB array in device global memory, reserved on every GPU
- *   that loads the library until the process exits.  Limit: 8 + 2 m n + n^2
+ *   that loads the library until the process exits.  Limit: 2 m n + n^2
  *   doubles (e.g. m = 2048, n = 448); larger sizes, or n > 2048, or m < n return
- *   TT_ERR_INVALID_ARG without touching the GPU.
+ *   TT_ERR_INVALID_ARG without touching the GPU.  The call queues one device-
+ *   to-device copy of A, the kernel (its job record passed as a kernel
+ *   argument) and two device-to-device copies of Q and R: no host-to-device
+ *   copy, so it does not wait for the stream.
  *   A (m x n, column-major), Q (m x n, column-major) and R (n x n, column-major)
  *   are device pointers of the current device; the work is queued on
  *   cuda_stream (NULL: legacy default stream) and the call returns without

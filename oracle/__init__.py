@@ -18,8 +18,6 @@ tantrg  the dense super-MPS tanTRG integrator: rho_h(beta0) = I - beta0 H/2,
         based exponential method"), 1-TDVP sweeps (Supplement, "Procedure of
         1-TDVP"), 2-TDVP growth sweeps (Supplement, "2-TDVP in the initial
         stage"), bilayer measurements (Supplement, Choi transformation).
-kernels one-shot references for single GPU entry points (one H_eff apply,
-        one environment update, one QR gauge step) on given dense inputs.
 
 Pins: see tests/test_oracle_*.py.  Every function names the passage it
 follows; where the paper is silent the reading taken is stated inline.

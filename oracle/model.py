@@ -203,8 +203,10 @@ def ed_spectrum(m: Model):
     return blocks
 
 
-def ed_thermo(m: Model, betas, beta0: float = 0.0, blocks=None) -> list[dict]:
-    """Exact thermodynamics of rho_h = exp(-(beta-beta0) H/2) (I - beta0 H/2).
+def ed_thermo(m: Model, betas, beta0: float = 0.0, blocks=None, order: int = 1) -> list[dict]:
+    """Exact thermodynamics of rho_h = exp(-(beta-beta0) H/2) (I - beta0 H/2)
+    (order = 1), or with the initial state sum_{k <= order} (-beta0 H/2)^k / k!
+    (the series-expansion initialisation, Supplement "Error analysis").
 
     With beta0 = 0 this is the Gibbs state (rho = rho_h rho_h^T = exp(-beta H)).
     With beta0 > 0 it is the exact image of the first-order initial state
@@ -235,7 +237,12 @@ def ed_thermo(m: Model, betas, beta0: float = 0.0, blocks=None) -> list[dict]:
     db = np.concatenate(dbl_all)
     out = []
     for beta in np.atleast_1d(betas):
-        g = 1.0 - beta0 * E / 2.0
+        g = np.zeros_like(E)
+        term = np.ones_like(E)
+        for k in range(order + 1):
+            if k:
+                term = term * (-beta0 * E / 2.0) / k
+            g = g + term
         logw = -(beta - beta0) * E + 2.0 * np.log(np.abs(g))
         mx = logw.max()
         w = np.exp(logw - mx)

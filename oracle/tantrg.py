@@ -242,6 +242,48 @@ def init_state(W: list, beta0: float, compress_cut: float = 1e-14) -> State:
     return st
 
 
+def init_state_series(W: list, beta0: float, order: int, compress_cut: float = 1e-14) -> State:
+    """rho_h(beta0) = sum_{k <= order} (-beta0 H / 2)^k / k!, the series-
+    expansion initial state (Supplement, "Error analysis of tanTRG": rho_0 =
+    sum_n (-tau_0 H)^n / n! with the SETTN technique; here tau_0 = beta0 / 2
+    because the MPO holds rho(beta/2)).  Built densely from the contracted MPO
+    of H (small systems only: 4^N x 4^N), cut into the super-MPS by successive
+    SVDs (singular values <= compress_cut * s_max dropped), then brought to the
+    same compact right-canonical form as init_state."""
+    from .mpo import mpo_to_dense
+    N = len(W)
+    H = mpo_to_dense(W)
+    rho = np.eye(H.shape[0])
+    term = np.eye(H.shape[0])
+    for k in range(1, order + 1):
+        term = term @ (-0.5 * beta0 * H) / k
+        rho = rho + term
+    # |rho>> with the pair (sigma_j, sigma'_j) per site, site 0 leftmost
+    T = rho.reshape((4,) * (2 * N)).transpose([x for j in range(N) for x in (j, N + j)])
+    A = []
+    rest = T.reshape(1, -1)
+    for j in range(N - 1):
+        Dl = rest.shape[0]
+        U, sv, Vt = np.linalg.svd(rest.reshape(Dl * 16, -1), full_matrices=False)
+        k = int(np.count_nonzero(sv > compress_cut * sv[0]))
+        A.append(U[:, :k].reshape(Dl, 4, 4, k))
+        rest = sv[:k, None] * Vt[:k]
+    A.append(rest.reshape(rest.shape[0], 4, 4, 1))
+    st = State(W=W, A=A)
+    _right_canonicalise(st)
+    for j in range(N - 1):
+        Dl, _, _, Dr = st.A[j].shape
+        U, sv, Vt = np.linalg.svd(st.A[j].reshape(Dl * 16, Dr), full_matrices=False)
+        k = int(np.count_nonzero(sv > compress_cut * sv[0]))
+        st.A[j] = U[:, :k].reshape(Dl, 4, 4, k)
+        st.A[j + 1] = np.tensordot(sv[:k, None] * Vt[:k], st.A[j + 1], axes=([1], [0]))
+    _right_canonicalise(st)
+    st.A[0] = _normalise(st, st.A[0])
+    st.beta = beta0
+    build_envs(st)
+    return st
+
+
 def pad_to_full_rank(st: State) -> State:
     """Embed the right-canonical state into bonds of the maximal dimension
     min(16^k, 16^(N-k)) by orthonormal completion (zero weight).  With every
@@ -457,12 +499,17 @@ def hermiticity_defect(st: State) -> float:
 # ----------------------------------------------------------------------------
 
 def run(W, beta0: float, dtau: float, beta_end: float, opts: TruncOpts, K: int = 8,
-        grow_until: float = 1.0, callback=None, max_grow_steps=None, pad_full: bool = False):
+        grow_until: float = 1.0, callback=None, max_grow_steps=None, pad_full: bool = False,
+        grow_ratio: float | None = None, taylor_order: int = 1):
     """Growth with 2-TDVP until every bond is saturated or beta >= grow_until,
     then 1-TDVP steps until beta >= beta_end (the hybrid scheme of the main
-    text with a linear grid).  ``callback(st, stage)`` runs after every step.
-    pad_full: start from the state padded to maximal bonds (no growth)."""
-    st = init_state(W, beta0)
+    text).  The growth grid is linear (steps of dtau) or, with grow_ratio,
+    exponential: beta -> grow_ratio * beta per step, the last step ending at
+    grow_until (main text, exponential grids for the two-site stage; Fig. S7
+    caption: beta_n = 2^(n/m) beta_0).  ``callback(st, stage)`` runs after every
+    step.  pad_full: start from the state padded to maximal bonds (no growth).
+    taylor_order > 1: start from the series-expansion state (init_state_series)."""
+    st = init_state(W, beta0) if taylor_order == 1 else init_state_series(W, beta0, taylor_order)
     if pad_full:
         pad_to_full_rank(st)
         max_grow_steps = 0
@@ -472,7 +519,8 @@ def run(W, beta0: float, dtau: float, beta_end: float, opts: TruncOpts, K: int =
         if saturated(st, opts.D_max) or st.beta >= grow_until - eps or (
                 max_grow_steps is not None and n_grow >= max_grow_steps):
             break
-        tdvp2_step(st, dtau, opts, K)
+        step = dtau if grow_ratio is None else min(st.beta * (grow_ratio - 1.0), grow_until - st.beta)
+        tdvp2_step(st, step, opts, K)
         n_grow += 1
         if callback:
             callback(st, "grow")

@@ -12,14 +12,17 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
+#include <string>
 
 #include <cudaTypedefs.h>
 
@@ -108,7 +111,8 @@ void upload(tt_ctx* c, const GemmPlan& p, DevGemmBuf& o) {
   o.host = p;
   o.checked = false;
   o.tc_checked = o.tc_ok = false;
-  o.ntiles128 = 0;
+  o.ntiles128 = o.ntilesp = 0;
+  o.choice = -1;
   for (int i = 0; i < 8; ++i) { o.key_p[i] = nullptr; o.key_lo[i] = 0; }
 }
 
@@ -145,10 +149,12 @@ void release(tt_ctx* c, DevGemmBuf& o) {
   dfree(c, o.buf);
   dfree(c, o.maps);
   dfree(c, o.tiles128);
+  dfree(c, o.tilesp);
   o.d = DevGemm();
   o.host = GemmPlan();
   o.checked = o.tc_checked = o.tc_ok = false;
-  o.ntiles128 = 0;
+  o.ntiles128 = o.ntilesp = 0;
+  o.choice = -1;
   for (int i = 0; i < 8; ++i) { o.key_p[i] = nullptr; o.key_lo[i] = 0; }
 }
 void release(tt_ctx* c, DevGatherBuf& o) { dfree(c, o.buf); o.d = DevGather(); o.host = GatherPlan(); o.checked = false; }
@@ -226,6 +232,16 @@ struct Eng {
 
   const Mpo& M() const { return r->mpo->mpo; }
   bool mixed() const { return r->nsplit > 0; }
+  // FP64 GEMM plans run on the exact-accumulation split kernel (tt_ozaki.cu)
+  // instead of FP64 FMA while set (env updates in the mixed modes, every
+  // contraction of the linear stage in TT_PREC_SPLIT_EXACT)
+  bool oz_now = false;
+  struct OzScope {
+    Eng& e;
+    bool saved;
+    OzScope(Eng& eng, bool on) : e(eng), saved(eng.oz_now) { e.oz_now = on; }
+    ~OzScope() { e.oz_now = saved; }
+  };
   double* dptr(DBuf& b) { return (double*)b.p; }
 
   void count(int n = 1) { r->launches_acc += n; }
@@ -256,9 +272,12 @@ struct Eng {
   // invalidates the precision-dependent plans and re-splits the environments
   // that are valid with the centre on site 0 (L[0], R[1..N]).
   void set_precision(int prec) {
-    const int ns = prec <= 0 ? 0 : (prec == 1 ? 2 : 3);
-    if (ns == r->nsplit) return;
+    const int ns = (prec == 1) ? 2 : (prec == 2 ? 3 : 0);
+    const bool oz = prec == 3;
+    if (ns == r->nsplit && oz == r->oz_all) return;
     drop_graph();
+    r->oz_all = oz;
+    if (ns == r->nsplit) return;
     r->nsplit = ns;
     for (auto& sp : r->sp) sp.valid = false;
     for (auto& bp : r->bp) bp.valid = false;
@@ -297,10 +316,21 @@ struct Eng {
     upload(c, s.h.s1, s.s1);
     upload(c, s.h.s2, s.s2);
     upload(c, s.h.s3, s.s3);
+    upload(c, s.h.s3l, s.s3l);
+    upload(c, s.h.r1, s.r1);
+    upload(c, s.h.r2, s.r2);
+    upload(c, s.h.r3, s.r3);
     ensure(c, r->T1, (size_t)std::max(s.h.t1_size, s.h.u1_size) * 8);
     ensure(c, r->T2, (size_t)std::max(s.h.t2_size, s.h.u2_size) * 8);
     s.valid = true;
     return s;
+  }
+  // environment updates in split-BF16 (else FP64 plans, also in mixed mode)
+  bool env_mixed() const { return mixed() && r->opts.env_precision == -1; }
+  // FP64 environment plans on the exact-accumulation split kernel
+  bool env_oz() const {
+    if (r->oz_all) return r->opts.env_precision != 1;
+    return mixed() && r->opts.env_precision == 0;
   }
   SiteDev& site_plan(int j) {
     SiteDev& s = r->sp[j];
@@ -506,16 +536,27 @@ struct Eng {
         if (sg.tA != 0 || sg.tB != 1 || sg.lda % 8 || sg.ldb % 8 || oa % 8 || ob % 8) g.tc_ok = false;
       }
       if (!g.tc_ok) return false;
-      std::vector<GTile> tiles;
+      // tile lists of both tcgen05 kernels: 128 x 128 and 128 x 64; the
+      // persistent kernel's list is ordered longest group first (more K
+      // chunks), so the long tiles start in the first wave
+      std::vector<GTile> tiles, tp;
+      std::vector<int> chunks(g.host.groups.size(), 0);
       for (size_t gi = 0; gi < g.host.groups.size(); ++gi) {
         const GGroup& gg = g.host.groups[gi];
-        for (int m0 = 0; m0 < gg.M; m0 += 128)
+        for (int si = gg.seg0; si < gg.seg1; ++si) chunks[gi] += (g.host.segs[si].K + 63) / 64;
+        for (int m0 = 0; m0 < gg.M; m0 += 128) {
           for (int n0 = 0; n0 < gg.N; n0 += 128) tiles.push_back(GTile{(int)gi, m0, n0, 0});
+          for (int n0 = 0; n0 < gg.N; n0 += 64) tp.push_back(GTile{(int)gi, m0, n0, 0});
+        }
       }
+      std::stable_sort(tp.begin(), tp.end(), [&](const GTile& a, const GTile& b2) { return chunks[a.g] > chunks[b2.g]; });
       ensure(c, g.tiles128, tiles.size() * sizeof(GTile) + 16);
+      ensure(c, g.tilesp, tp.size() * sizeof(GTile) + 16);
       if (!tiles.empty())
         CK(cudaMemcpyAsync(g.tiles128.p, tiles.data(), tiles.size() * sizeof(GTile), cudaMemcpyHostToDevice, st));
+      if (!tp.empty()) CK(cudaMemcpyAsync(g.tilesp.p, tp.data(), tp.size() * sizeof(GTile), cudaMemcpyHostToDevice, st));
       g.ntiles128 = (int)tiles.size();
+      g.ntilesp = (int)tp.size();
     }
     if (!g.tc_ok) return false;
     // the maps depend only on the slots the A and B operands live in
@@ -542,14 +583,14 @@ struct Eng {
       return false;
     }
     const size_t nseg = g.host.segs.size();
-    std::vector<CUtensorMap> maps(2 * nseg);
+    std::vector<CUtensorMap> maps(3 * nseg);
     std::vector<int> seg_group(nseg, 0);
     for (size_t gi = 0; gi < g.host.groups.size(); ++gi)
       for (int si = g.host.groups[gi].seg0; si < g.host.groups[gi].seg1; ++si) seg_group[si] = (int)gi;
     for (size_t si = 0; si < nseg; ++si) {
       const GSeg& sg = g.host.segs[si];
       const GGroup& gg = g.host.groups[seg_group[si]];
-      for (int w = 0; w < 2; ++w) {
+      for (int w = 0; w < 3; ++w) {  // A (box 64 x 128), B (64 x 128), B (64 x 64)
         const Ref ref = w == 0 ? sg.A : sg.B;
         const int sl = (int)(ref >> 56);
         const int64_t off = (int64_t)(ref & 0x00FFFFFFFFFFFFFFull);
@@ -557,10 +598,10 @@ struct Eng {
         if (!b.p[sl] || lo % 8 || sg.K < 1) { g.tc_ok = false; return false; }
         cuuint64_t dims[3] = {(cuuint64_t)sg.K, (cuuint64_t)std::max(1, w == 0 ? gg.M : gg.N), (cuuint64_t)r->nsplit};
         cuuint64_t strides[2] = {(cuuint64_t)(w == 0 ? sg.lda : sg.ldb) * 2, (cuuint64_t)lo * 2};
-        cuuint32_t box[3] = {64, 128, 1};
+        cuuint32_t box[3] = {64, (cuuint32_t)(w == 2 ? 64 : 128), 1};
         cuuint32_t estr[3] = {1, 1, 1};
         void* base = (char*)b.p[sl] + off * 2;
-        CUresult cr = encode(&maps[2 * si + w], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+        CUresult cr = encode(&maps[3 * si + w], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr != CUDA_SUCCESS) {
@@ -579,17 +620,91 @@ struct Eng {
     return true;
   }
 
-  void gemm(DevGemmBuf& g, const Bases& b, bool use_mixed, int kind = 4) {
-    const long e = prof_begin(kind, g.d.flops);
-    if (use_mixed && r->use_tc && prep_tc(g, b)) {
-      if (!r->tcerr.p) {
-        ensure(c, r->tcerr, 16);
-        CK(cudaMemsetAsync(r->tcerr.p, 0, 16, st));
-      }
+  // one launch of a split-BF16 plan on kernel k (tcgen05 kernels need prep_tc)
+  void launch_split(DevGemmBuf& g, const Bases& b, int k) {
+    if (k != TK_MMA64 && !r->tcerr.p) {
+      ensure(c, r->tcerr, 16);
+      CK(cudaMemsetAsync(r->tcerr.p, 0, 16, st));
+    }
+    if (k == TK_TC128)
       CK(launch_gemm_tc(g.d.groups, g.d.segs, (const GTile*)g.tiles128.p, g.ntiles128, g.maps.p, b, r->nsplit,
-                        (int*)r->tcerr.p, st));
-    } else if (use_mixed) {
+                        (int*)r->tcerr.p, c->wait_ns, st));
+    else if (k == TK_TCP128X64)
+      CK(launch_gemm_tcp(g.d.groups, g.d.segs, (const GTile*)g.tilesp.p, g.ntilesp, g.maps.p, b, r->nsplit,
+                         (int*)r->tcerr.p, c->wait_ns, st));
+    else
       CK(launch_gemm_bf16(g.d, b, r->nsplit, st));
+  }
+
+  // Tile-shape autotuner: the first uncaptured launch of a split-BF16 plan
+  // times every eligible kernel (128 x 128 tcgen05, persistent 128 x 64
+  // tcgen05, 64 x 64 mma.sync) with CUDA events, second of two runs each,
+  // and keeps the fastest for the plan; plans of the same shape signature
+  // (split levels, groups, tiles, K chunks) reuse the choice process-wide.
+  // Every candidate overwrites the plan's whole output (no plan here
+  // accumulates into C), and the chosen kernel runs last, so the output is
+  // the chosen kernel's.  TT_GEMM=tc|tcp|mma forces one kernel.
+  int tune(DevGemmBuf& g, const Bases& b, bool tc) {
+    static const int forced = [] {
+      const char* v = std::getenv("TT_GEMM");
+      if (!v) return -1;
+      if (!std::strcmp(v, "tc")) return (int)TK_TC128;
+      if (!std::strcmp(v, "tcp")) return (int)TK_TCP128X64;
+      if (!std::strcmp(v, "mma")) return (int)TK_MMA64;
+      return -1;
+    }();
+    if (forced >= 0) return (forced == TK_MMA64 || tc) ? forced : (int)TK_MMA64;
+    if (!tc) return TK_MMA64;
+    if (r->capturing) return TK_TCP128X64;  // plans are tuned in the uncaptured step; this is a fallback
+    long long chunks = 0, msum = 0, nsum = 0;
+    for (const GSeg& sg : g.host.segs) chunks += (sg.K + 63) / 64;
+    for (const GGroup& gg : g.host.groups) { msum += gg.M; nsum += gg.N; }
+    char key[160];
+    std::snprintf(key, sizeof key, "%d/%zu/%zu/%d/%lld/%lld/%lld", r->nsplit, g.host.groups.size(), g.host.segs.size(),
+                  g.ntiles128, chunks, msum, nsum);
+    static std::mutex mu;
+    static std::map<std::string, int> cache;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      auto it = cache.find(key);
+      if (it != cache.end()) return it->second;
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = TK_MMA64;
+    float best_ms = 1e30f;
+    for (int k : {(int)TK_MMA64, (int)TK_TC128, (int)TK_TCP128X64}) {
+      launch_split(g, b, k);
+      CK(cudaEventRecord(e0, st));
+      launch_split(g, b, k);
+      CK(cudaEventRecord(e1, st));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) { best_ms = ms; best = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    check_tc();
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best;
+    return best;
+  }
+
+  void gemm(DevGemmBuf& g, const Bases& b, bool use_mixed, int kind = 4) {
+    if (use_mixed) {
+      const bool tc = r->use_tc && prep_tc(g, b);
+      if (g.choice < 0 || (!tc && g.choice != TK_MMA64)) {
+        g.choice = tune(g, b, tc);
+        ++r->tuned[g.choice];
+      }
+    }
+    const long e = prof_begin(kind, g.d.flops);
+    if (use_mixed) {
+      launch_split(g, b, g.choice);
+    } else if (oz_now) {
+      CK(launch_gemm_oz(g.d, b, st));
     } else {
       CK(launch_gemm_f64(g.d, b, st));
     }
@@ -653,7 +768,7 @@ struct Eng {
     const int el = mixed() ? 2 * r->nsplit : 8;
     if (left_env_in) { need(r->L[j], r->Lsize[j] * 8, "L"); if (mixed()) need(r->Lsp[j], r->Lpsize[j] * el, "Lsp"); }
     if (right_env_in) { need(r->R[j + 1], r->Rsize[j + 1] * 8, "R"); if (mixed()) need(r->Rsp[j + 1], r->Rpsize[j + 1] * el, "Rsp"); }
-    if (mixed()) need(r->Xs, std::max<int64_t>(s.h.xt_size, 1) * 2 * r->nsplit, "Xs");
+    if (mixed() && s.h.xt_size > 0) need(r->Xs, s.h.xt_size * 2 * r->nsplit, "Xs");  // split-BF16 plans only
     if (left_env_in && r->Lsize[j] != make_env_layout(r->bond[j], M().chan[j]).size) throw Err{TT_ERR_STATE, "stale L"};
     if (right_env_in && r->Rsize[j + 1] != make_env_layout(r->bond[j + 1], M().chan[j + 1]).size) throw Err{TT_ERR_STATE, "stale R"};
     need(r->T1, std::max(s.h.t1_size, s.h.u1_size) * 8, "T1");
@@ -682,6 +797,7 @@ struct Eng {
       gather(s.s2, b, 1, r->nsplit);
       gemm(s.s3, b, true, 0);
     } else {
+      OzScope oz(*this, r->oz_all && !force_fp64);
       b.p[S_X] = (void*)x;
       b.p[S_L] = r->L[j].p;
       b.p[S_R] = r->R[j + 1].p;
@@ -732,6 +848,7 @@ struct Eng {
       b.p[S_T2] = r->T2.p; b.lo[S_T2] = bd.h.tp_size;
       gemm(bd.b2, b, true, 2);
     } else {
+      OzScope oz(*this, r->oz_all);
       b.p[S_X] = (void*)x;
       b.p[S_L] = r->L[k].p;
       b.p[S_R] = r->R[k].p;
@@ -744,7 +861,7 @@ struct Eng {
 
   // L[j+1] from L[j] and the left-canonical A_j
   void update_left_env(int j) {
-    SiteDev& s = site_plan(j);
+    SiteDev& s = env_mixed() ? site_plan(j) : site_plan_fp64(j);
     ensure_env(r->L, r->Lsp, r->Lsize, j + 1);
     need_site(j, s, true, false);
     need(r->A[j], s.h.lay.size * 8, "A");
@@ -752,7 +869,7 @@ struct Eng {
     b.p[S_Y] = r->L[j + 1].p;
     b.p[S_T1] = r->T1.p;
     b.p[S_T2] = r->T2.p;
-    if (mixed()) {
+    if (env_mixed()) {
       int64_t n = s.h.lay.size;
       split_x_transposed(s, dptr(r->A[j]));
       split(dptr(r->A[j]), n, r->Xn.p);
@@ -764,6 +881,7 @@ struct Eng {
       gather(s.s2, b, 1, r->nsplit);
       gemm(s.s3l, b, true, 1);
     } else {
+      OzScope oz(*this, env_oz());
       b.p[S_X] = r->A[j].p;
       b.p[S_L] = r->L[j].p;
       gemm(s.s1, b, false, 1);
@@ -776,7 +894,7 @@ struct Eng {
 
   // R[j] from R[j+1] and the right-canonical A_j
   void update_right_env(int j) {
-    SiteDev& s = site_plan(j);
+    SiteDev& s = env_mixed() ? site_plan(j) : site_plan_fp64(j);
     ensure_env(r->R, r->Rsp, r->Rsize, j);
     need_site(j, s, false, true);
     need(r->A[j], s.h.lay.size * 8, "A");
@@ -784,7 +902,7 @@ struct Eng {
     b.p[S_Y] = r->R[j].p;
     b.p[S_T1] = r->T1.p;
     b.p[S_T2] = r->T2.p;
-    if (mixed()) {
+    if (env_mixed()) {
       int64_t n = s.h.lay.size;
       split(dptr(r->A[j]), n, r->Xn.p);
       b.p[S_AUX] = r->Xn.p; b.lo[S_AUX] = n;
@@ -794,6 +912,7 @@ struct Eng {
       gather(s.r2, b, 1, r->nsplit);
       gemm(s.r3, b, true, 1);
     } else {
+      OzScope oz(*this, env_oz());
       b.p[S_X] = r->A[j].p;
       b.p[S_R] = r->R[j + 1].p;
       gemm(s.r1, b, false, 1);
@@ -1014,6 +1133,117 @@ struct Eng {
     CK(k_normalise_inplace(dptr(r->A[0]), r->lay[0].size, dptr(r->partial), ks, (RhoScalars*)r->rs.p, st));
     build_boundary_envs();
     for (int j = N - 1; j >= 1; --j) update_right_env(j);
+    CK(cudaStreamSynchronize(st));
+  }
+
+  // One Horner step of the series-expansion initial state (SETTN, Supplement
+  // "Error analysis": rho_0 = sum_n (-tau_0 H)^n / n!):  rho <- I + alpha H
+  // rho, with rho = exp(logscale) x (the super-MPS on the device).  The
+  // product H rho is local (W_j acts on sigma of A_j; bond space (w, a) of the
+  // MPO channel and the state's bond), the identity is added as a direct sum
+  // (one extra state of charge 0 on every interior bond; the first site's
+  // right bond and the last site's left bond are concatenated), assembled on
+  // the host, uploaded and compressed exactly like the first-order state.
+  void horner_step(double alpha) {
+    const Mpo& m = M();
+    const int N = r->N;
+    const LocalSpace& ls = m.ls;
+    const int d = ls.d;
+    CK(cudaStreamSynchronize(st));
+    std::vector<std::vector<double>> A(N);
+    for (int j = 0; j < N; ++j) {
+      A[j].resize(r->lay[j].size);
+      CK(cudaMemcpyAsync(A[j].data(), r->A[j].p, A[j].size() * 8, cudaMemcpyDeviceToHost, st));
+    }
+    RhoScalars rs;
+    CK(cudaMemcpyAsync(&rs, r->rs.p, sizeof(rs), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double coef = alpha * std::exp(rs.logscale);
+    // new bonds: interior k: identity state (charge 0) first, then (w, a)
+    std::vector<Bond> nb(N + 1);
+    // place[k][w][s] = (new sector, first index) of the states (w, a in sector s)
+    std::vector<std::vector<std::vector<std::pair<int, int>>>> place(N + 1);
+    std::vector<std::pair<int, int>> ident(N + 1, {-1, -1});
+    for (int k = 0; k <= N; ++k) {
+      const Bond& B = r->bond[k];
+      const bool interior = k > 0 && k < N;
+      std::map<Q, int> dim;
+      if (interior) dim[Q{0, 0}] += 1;
+      for (size_t w = 0; w < m.chan[k].size(); ++w)
+        for (int q = 0; q < B.nsec(); ++q) dim[m.chan[k][w] + B.q[q]] += B.dim[q];
+      for (auto& kv : dim) { nb[k].q.push_back(kv.first); nb[k].dim.push_back(kv.second); }
+      std::map<Q, int> next;
+      if (interior) { ident[k] = {nb[k].find(Q{0, 0}), 0}; next[Q{0, 0}] = 1; }
+      place[k].assign(m.chan[k].size(), std::vector<std::pair<int, int>>(B.nsec()));
+      for (size_t w = 0; w < m.chan[k].size(); ++w)
+        for (int q = 0; q < B.nsec(); ++q) {
+          const Q c = m.chan[k][w] + B.q[q];
+          place[k][w][q] = {nb[k].find(c), next[c]};
+          next[c] += B.dim[q];
+        }
+    }
+    if (nb[0].total() != 1 || nb[N].total() != 1) throw Err{TT_ERR_STATE, "series step: boundary bonds must stay one-dimensional"};
+    std::vector<SiteLayout> nl(N);
+    std::vector<std::vector<double>> P(N);
+    for (int j = 0; j < N; ++j) {
+      nl[j] = make_site_layout(nb[j], nb[j + 1], ls);
+      P[j].assign(nl[j].size, 0.0);
+      const SiteLayout& S = r->lay[j];
+      const SiteLayout& T = nl[j];
+      auto at = [&](int L, int li, int pair, int R, int ri) -> double& {
+        const int p = ls.sec_of[pair], pos = ls.pos_of[pair];
+        const int bi = T.block_of(L, p);
+        if (bi < 0 || T.blk[bi].r != R) throw Err{TT_ERR_STATE, "series step: block outside the charge structure"};
+        const SiteBlock& B = T.blk[bi];
+        return P[j][B.off + ((int64_t)li * B.m + pos) * B.dr + ri];
+      };
+      // H rho: W_j[wl, sig, tau, wr] A_j[a, (tau, sp), b]
+      const double scale = (j == 0) ? coef : 1.0;
+      for (const MpoTerm& t : m.site[j].terms)
+        for (const SiteBlock& b : S.blk)
+          for (int pos = 0; pos < b.m; ++pos) {
+            const int tau = ls.pairs[b.p][pos].first, sp = ls.pairs[b.p][pos].second;
+            if (tau != t.tau) continue;
+            const auto pl = place[j][t.wl][b.l], pr = place[j + 1][t.wr][b.r];
+            for (int a = 0; a < b.dl; ++a)
+              for (int c2 = 0; c2 < b.dr; ++c2)
+                at(pl.first, pl.second + a, t.sig * d + sp, pr.first, pr.second + c2) +=
+                    scale * t.v * A[j][b.off + ((int64_t)a * b.m + pos) * b.dr + c2];
+          }
+      // + I: one identity state on the interior bonds (boundary bonds shared)
+      const int Li = j == 0 ? 0 : ident[j].first, li = j == 0 ? 0 : ident[j].second;
+      const int Ri = j == N - 1 ? 0 : ident[j + 1].first, ri = j == N - 1 ? 0 : ident[j + 1].second;
+      for (int sg = 0; sg < d; ++sg) at(Li, li, sg * d + sg, Ri, ri) += 1.0;
+    }
+    // replace the state
+    for (int k = 0; k <= N; ++k) r->bond[k] = nb[k];
+    for (int k = 0; k <= N; ++k) invalidate_bond(k);
+    for (int j = 0; j < N; ++j) {
+      r->lay[j] = nl[j];
+      ensure_site_buf(j);
+      CK(cudaMemcpyAsync(r->A[j].p, P[j].data(), P[j].size() * 8, cudaMemcpyHostToDevice, st));
+    }
+    rs.logscale = 0.0;
+    CK(cudaMemcpyAsync(r->rs.p, &rs, sizeof(rs), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    right_canonicalise_shrinking();
+    compress_sweep(1e-14);
+    right_canonicalise_shrinking();
+    ensure_vec_capacity();
+    KrylovState* ks = (KrylovState*)r->ks.p;
+    CK(k_normalise_inplace(dptr(r->A[0]), r->lay[0].size, dptr(r->partial), ks, (RhoScalars*)r->rs.p, st));
+    CK(cudaStreamSynchronize(st));
+  }
+
+  // rho_0 = sum_{n <= order} (-beta0 H / 2)^n / n! by Horner's rule:
+  // P_{order-1} = I - (beta0 / (2 order)) H (the compact first-order state),
+  // P_k = I - (beta0 / (2 (k + 1))) H P_{k+1}, rho_0 = P_0.
+  void init_series(double beta0, int order) {
+    init_state(beta0 / order);
+    for (int k = order - 2; k >= 0; --k) horner_step(-beta0 / (2.0 * (k + 1)));
+    r->beta = beta0;
+    build_boundary_envs();
+    for (int j = r->N - 1; j >= 1; --j) update_right_env(j);
     CK(cudaStreamSynchronize(st));
   }
 
@@ -1469,8 +1699,8 @@ struct Eng {
     CK(cudaMemcpyAsync(&rs, r->rs.p, sizeof(rs), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     dfree(c, part2);
+    check_tc();  // an aborted GEMM leaves garbage behind: report the cause first
     if (rs.bad) throw Err{TT_ERR_NUMERIC, "non-finite or zero norm in a Krylov update"};
-    check_tc();
     double nrm2 = hv[3];
     out->beta = r->beta;
     out->energy_per_site = hv[2] / nrm2 / N;
@@ -1866,8 +2096,8 @@ struct Eng {
     RhoScalars rs;
     CK(cudaMemcpyAsync(&rs, r->rs.p, sizeof(rs), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    check_tc();  // an aborted GEMM leaves garbage behind: report the cause first
     if (rs.bad) throw Err{TT_ERR_NUMERIC, "non-finite or zero norm in a Krylov update"};
-    check_tc();
   }
   void check_tc() {
     if (!r->tcerr.p) return;
@@ -1968,8 +2198,9 @@ void free_rho(tt_rho* r) {
 }
 
 bool valid_opts(const tt_run_opts* o) {
-  return o && o->D_max >= 1 && o->krylov_dim >= 1 && o->krylov_dim <= 16 && o->precision >= 0 && o->precision <= 2 &&
-         o->growth_precision >= -1 && o->growth_precision <= 2 && o->svd_cut >= 0 && o->degen_tol >= 0;
+  return o && o->D_max >= 1 && o->krylov_dim >= 1 && o->krylov_dim <= 16 && o->precision >= 0 && o->precision <= 3 &&
+         o->growth_precision >= -1 && o->growth_precision <= 3 && o->svd_cut >= 0 && o->degen_tol >= 0 &&
+         o->env_precision >= -1 && o->env_precision <= 1;
 }
 
 }  // namespace
@@ -2008,6 +2239,12 @@ void tt_ctx_destroy(tt_ctx* ctx) {
 }
 
 const char* tt_last_error(const tt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+tt_status tt_ctx_set_wait_limit(tt_ctx* ctx, double seconds) {
+  if (!ctx || !std::isfinite(seconds) || seconds < 0 || seconds > 60) return TT_ERR_INVALID_ARG;
+  ctx->wait_ns = (long long)(seconds * 1e9);
+  return TT_OK;
+}
 
 tt_status tt_hubbard_mpo_create(tt_ctx* ctx, const tt_model* m, tt_mpo** out) {
   if (!ctx || !m || !out) return TT_ERR_INVALID_ARG;
@@ -2057,7 +2294,8 @@ tt_status tt_mpo_channel_charge(const tt_mpo* mpo, int k, int w, int* qn, int* q
 
 tt_status tt_rho_create(tt_ctx* ctx, const tt_mpo* mpo, double beta0, int taylor_order, const tt_run_opts* opts,
                         tt_rho** out) {
-  if (!ctx || !mpo || !out || !valid_opts(opts) || taylor_order != 1 || !(beta0 > 0) || !std::isfinite(beta0)) {
+  if (!ctx || !mpo || !out || !valid_opts(opts) || taylor_order < 1 || taylor_order > 8 || !(beta0 > 0) ||
+      !std::isfinite(beta0)) {
     if (ctx) ctx->err = "invalid argument to tt_rho_create";
     return TT_ERR_INVALID_ARG;
   }
@@ -2068,11 +2306,13 @@ tt_status tt_rho_create(tt_ctx* ctx, const tt_mpo* mpo, double beta0, int taylor
   r->mpo = mpo;
   r->opts = *opts;
   r->N = mpo->mpo.N;
-  r->nsplit = opts->growth_precision <= 0 ? 0 : (opts->growth_precision == 1 ? 2 : 3);
+  r->nsplit = opts->growth_precision == 1 ? 2 : (opts->growth_precision == 2 ? 3 : 0);
+  r->oz_all = opts->growth_precision == 3;
   tt_status s = guarded(ctx, r, [&] {
     alloc_rho_arrays(r);
     Eng e(r);
-    e.init_state(beta0);
+    if (taylor_order == 1) e.init_state(beta0);
+    else e.init_series(beta0, taylor_order);
   });
   if (s != TT_OK) {
     free_rho(r);
@@ -2111,6 +2351,23 @@ tt_status tt_rho_grow(tt_rho* rho, const tt_mpo* mpo, double dtau, double beta_m
   });
 }
 
+tt_status tt_rho_grow_exp(tt_rho* rho, const tt_mpo* mpo, double ratio, double beta_max, double* beta_reached) {
+  if (!rho || mpo != rho->mpo || !(ratio > 1.0) || !(ratio <= 4.0) || !std::isfinite(beta_max))
+    return TT_ERR_INVALID_ARG;
+  return guarded(rho->ctx, rho, [&] {
+    Eng e(rho);
+    e.set_precision(rho->opts.growth_precision);
+    while (rho->beta < beta_max - 1e-12 && !e.saturated()) {
+      const double dtau = std::min(rho->beta * (ratio - 1.0), beta_max - rho->beta);
+      e.grow_sweep_lr(dtau / 4);
+      e.grow_sweep_rl(dtau / 4);
+      rho->beta += dtau;
+      e.check_bad();
+    }
+    if (beta_reached) *beta_reached = rho->beta;
+  });
+}
+
 tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps) {
   if (!rho || mpo != rho->mpo || !(dtau > 0) || n_steps < 0) return TT_ERR_INVALID_ARG;
   return guarded(rho->ctx, rho, [&] {
@@ -2130,7 +2387,7 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
       CK(cudaEventRecord(rho->ev0, st));
     }
     if (rho->graph && (rho->graph_dtau != dtau || rho->graph_prof != rho->prof ||
-                       rho->graph_buf_gen != rho->ctx->buf_gen))
+                       rho->graph_buf_gen != rho->ctx->buf_gen || rho->graph_wait_ns != rho->ctx->wait_ns))
       e.drop_graph();
     int s = 0;
     if (!rho->graph && rho->use_graph && n_steps > 0 && st != nullptr && !rho->stats_pending) {
@@ -2181,6 +2438,7 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
       }
       rho->graph_dtau = dtau;
       rho->graph_prof = rho->prof;
+      rho->graph_wait_ns = rho->ctx->wait_ns;
       rho->graph_buf_gen = rho->ctx->buf_gen;
       rho->graph_heff_flops = rho->heff_flops_acc - hf;
       rho->graph_step_flops = rho->step_flops_acc - sf;
@@ -2301,6 +2559,9 @@ tt_status tt_stats_get(const tt_rho* rho_c, tt_stats* out) {
   for (auto& b : rho->bond) { mb = std::max<int>(mb, (int)b.total()); ns = std::max(ns, b.nsec()); }
   out->max_bond = mb;
   out->n_sectors_max = ns;
+  out->tuned_tc128 = rho->tuned[TK_TC128];
+  out->tuned_tcp128x64 = rho->tuned[TK_TCP128X64];
+  out->tuned_mma64 = rho->tuned[TK_MMA64];
   return TT_OK;
 }
 
@@ -2354,22 +2615,16 @@ tt_status tt_layout_sizes(const tt_mpo* mpo, int site, const int* nsec_lr, const
   return TT_OK;
 }
 
-tt_status tt_heff_apply_host(tt_ctx* ctx, const tt_mpo* mpo, int site, int precision, const int* nsec_lr,
-                             const int* qn, const int* qs, const int* qd, const double* Lh, const double* Rh,
-                             const double* xh, double* yh) {
-  if (!ctx || !mpo || !Lh || !Rh || !xh || !yh || precision < 0 || precision > 2) return TT_ERR_INVALID_ARG;
-  Bond BL, BR;
-  if (!read_bonds_lr(mpo, site, nsec_lr, qn, qs, qd, BL, BR)) {
-    ctx->err = "invalid sector tables";
-    return TT_ERR_INVALID_ARG;
-  }
+static tt_status heff_apply_impl(tt_ctx* ctx, const tt_mpo* mpo, int site, int precision, const Bond& BL,
+                                 const Bond& BR, const double* Lh, const double* Rh, const double* xh, double* yh) {
   tt_rho* r = new (std::nothrow) tt_rho();
   if (!r) return TT_ERR_OOM;
   r->ctx = ctx;
   r->mpo = mpo;
-  r->opts = tt_run_opts{1, 1, precision, precision, 1e-12, 1e-10};
+  r->opts = tt_run_opts{1, 1, precision, precision, 1e-12, 1e-10, 0};
   r->N = mpo->mpo.N;
-  r->nsplit = precision == 0 ? 0 : (precision == 1 ? 2 : 3);
+  r->nsplit = (precision == 1) ? 2 : (precision == 2 ? 3 : 0);
+  r->oz_all = precision == 3;
   tt_status s = guarded(ctx, nullptr, [&] {
     alloc_rho_arrays(r);
     r->bond.assign(r->N + 1, Bond());
@@ -2391,12 +2646,82 @@ tt_status tt_heff_apply_host(tt_ctx* ctx, const tt_mpo* mpo, int site, int preci
     e.apply_site(site, (const double*)r->A[site].p, (double*)r->W.p);
     CK(cudaMemcpyAsync(yh, r->W.p, nx * 8, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
+    e.check_tc();
   });
   cudaStreamSynchronize(ctx->st);
   free_rho(r);
   cudaStreamSynchronize(ctx->st);
   delete r;
   return s;
+}
+
+tt_status tt_heff_apply_host(tt_ctx* ctx, const tt_mpo* mpo, int site, int precision, const int* nsec_lr,
+                             const int* qn, const int* qs, const int* qd, const double* Lh, const double* Rh,
+                             const double* xh, double* yh) {
+  if (!ctx || !mpo || !Lh || !Rh || !xh || !yh || precision < 0 || precision > 3) return TT_ERR_INVALID_ARG;
+  Bond BL, BR;
+  if (!read_bonds_lr(mpo, site, nsec_lr, qn, qs, qd, BL, BR)) {
+    ctx->err = "invalid sector tables";
+    return TT_ERR_INVALID_ARG;
+  }
+  return heff_apply_impl(ctx, mpo, site, precision, BL, BR, Lh, Rh, xh, yh);
+}
+
+tt_status tt_heff_apply_terms_host(tt_ctx* ctx, int nw_l, const int* chl_qn, const int* chl_qs, int nw_r,
+                                   const int* chr_qn, const int* chr_qs, int nterms, const int* t_wl, const int* t_wr,
+                                   const int* t_sig, const int* t_tau, const double* t_val, int precision,
+                                   const int* nsec_lr, const int* qn, const int* qs, const int* qd, const double* Lh,
+                                   const double* Rh, const double* xh, double* yh) {
+  if (!ctx || !chl_qn || !chl_qs || !chr_qn || !chr_qs || nw_l < 1 || nw_r < 1 || nw_l > 4096 || nw_r > 4096 ||
+      nterms < 0 || (nterms > 0 && (!t_wl || !t_wr || !t_sig || !t_tau || !t_val)) || !Lh || !Rh || !xh || !yh ||
+      precision < 0 || precision > 3)
+    return TT_ERR_INVALID_ARG;
+  tt_mpo m;
+  m.ctx = ctx;
+  m.mpo.N = 1;
+  m.mpo.Lx = 1;
+  m.mpo.Wy = 1;
+  m.mpo.ls = hubbard_site_space();
+  m.mpo.chan.assign(2, std::vector<Q>());
+  for (int w = 0; w < nw_l; ++w) m.mpo.chan[0].push_back(Q{chl_qn[w], chl_qs[w]});
+  for (int w = 0; w < nw_r; ++w) m.mpo.chan[1].push_back(Q{chr_qn[w], chr_qs[w]});
+  m.mpo.start_ch.assign(2, -1);
+  m.mpo.done_ch.assign(2, -1);
+  MpoSite site;
+  const LocalSpace& ls = m.mpo.ls;
+  for (int i = 0; i < nterms; ++i) {
+    const int wl = t_wl[i], wr = t_wr[i], sg = t_sig[i], ta = t_tau[i];
+    if (wl < 0 || wl >= nw_l || wr < 0 || wr >= nw_r || sg < 0 || sg >= ls.d || ta < 0 || ta >= ls.d ||
+        !std::isfinite(t_val[i]) || m.mpo.chan[1][wr] != m.mpo.chan[0][wl] + ls.q[sg] - ls.q[ta]) {
+      ctx->err = "invalid MPO term " + std::to_string(i) + " (index out of range, non-finite value, or channel " +
+                 "charges violating c_wr = c_wl + q(sig) - q(tau))";
+      return TT_ERR_INVALID_ARG;
+    }
+    site.terms.push_back(MpoTerm{wl, wr, sg, ta, t_val[i]});
+  }
+  std::sort(site.terms.begin(), site.terms.end(), [](const MpoTerm& a, const MpoTerm& b) {
+    return std::make_tuple(a.wr, a.sig, a.wl, a.tau) < std::make_tuple(b.wr, b.sig, b.wl, b.tau);
+  });
+  m.mpo.site.push_back(site);
+  Bond BL, BR;
+  if (!read_bonds_lr(&m, 0, nsec_lr, qn, qs, qd, BL, BR)) {
+    ctx->err = "invalid sector tables";
+    return TT_ERR_INVALID_ARG;
+  }
+  return heff_apply_impl(ctx, &m, 0, precision, BL, BR, Lh, Rh, xh, yh);
+}
+
+tt_status tt_layout_sizes_terms(int nw_l, const int* chl_qn, const int* chl_qs, int nw_r, const int* chr_qn,
+                                const int* chr_qs, const int* nsec_lr, const int* qn, const int* qs, const int* qd,
+                                int64_t* x_size, int64_t* l_size, int64_t* r_size) {
+  if (!chl_qn || !chl_qs || !chr_qn || !chr_qs || nw_l < 1 || nw_r < 1) return TT_ERR_INVALID_ARG;
+  tt_mpo m;
+  m.mpo.N = 1;
+  m.mpo.ls = hubbard_site_space();
+  m.mpo.chan.assign(2, std::vector<Q>());
+  for (int w = 0; w < nw_l; ++w) m.mpo.chan[0].push_back(Q{chl_qn[w], chl_qs[w]});
+  for (int w = 0; w < nw_r; ++w) m.mpo.chan[1].push_back(Q{chr_qn[w], chr_qs[w]});
+  return tt_layout_sizes(&m, 0, nsec_lr, qn, qs, qd, x_size, l_size, r_size);
 }
 
 static const char kMagic[8] = {'T', 'T', 'R', 'H', 'O', '0', '0', '1'};

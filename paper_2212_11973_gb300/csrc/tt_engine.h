@@ -20,6 +20,8 @@ struct tt_ctx {
   bool has_cb = false;
   std::string err;
   cusolverDnHandle_t sol = nullptr;
+  // time budget of every bounded device wait (tcgen05 GEMM mbarriers), ns
+  long long wait_ns = 2000000000ll;
 };
 
 struct tt_mpo {
@@ -53,11 +55,16 @@ struct DevGemmBuf {
   bool checked = false;
   // tcgen05 path: eligibility, 128 x 128 tile list, per-segment tensor maps
   bool tc_checked = false, tc_ok = false;
-  DBuf maps, tiles128;
-  int ntiles128 = 0;
+  DBuf maps, tiles128, tilesp;
+  int ntiles128 = 0, ntilesp = 0;  // 128 x 128 tiles (tc), 128 x 64 tiles (persistent tc)
+  // autotuned kernel of a split-BF16 plan: -1 not chosen yet, else a TcKernel
+  int choice = -1;
   void* key_p[8] = {nullptr};
   long long key_lo[8] = {0};
 };
+// Kernels a split-BF16 GEMM plan can run on (chosen per plan by timing).
+enum TcKernel { TK_TC128 = 0, TK_TCP128X64 = 1, TK_MMA64 = 2, TK_N = 3 };
+
 struct DevGatherBuf {
   DevGather d;
   DBuf buf;
@@ -126,7 +133,8 @@ struct tt_rho {
   const tt_mpo* mpo = nullptr;
   tt_run_opts opts{};
   int N = 0;
-  int nsplit = 0;  // 0 = FP64
+  int nsplit = 0;  // 0 = FP64 operand layouts
+  bool oz_all = false;  // TT_PREC_SPLIT_EXACT: FP64 plans on the exact-accumulation split kernel
   bool poisoned = false;
   double beta = 0.0;
   std::vector<tt::Bond> bond;           // N + 1
@@ -159,6 +167,7 @@ struct tt_rho {
   cudaGraphExec_t graph = nullptr;
   double graph_dtau = 0.0;
   bool graph_prof = false;
+  long long graph_wait_ns = 0;            // wait budget baked into the captured launches
   double graph_heff_flops = 0, graph_step_flops = 0;
   long long graph_launches = 0;
   bool use_graph = true;
@@ -177,4 +186,5 @@ struct tt_rho {
   double heff_flops_acc = 0, step_flops_acc = 0;
   long long launches_acc = 0;
   long long qr_sectors_acc = 0, graph_qr_sectors = 0;
+  long long tuned[tt::TK_N] = {0, 0, 0};  // plans per autotuned kernel choice
 };

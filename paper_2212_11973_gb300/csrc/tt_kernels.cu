@@ -635,11 +635,19 @@ __global__ void nrm_finalize(const double* partial, int nblk, KrylovState* ks, R
 constexpr int QRT = 256;
 constexpr int QR_MAXN = 2048;
 
+__device__ __forceinline__ void qr_one(const QrJob J, double* __restrict__ ws);
+
 __global__ void __launch_bounds__(QRT) qr_kernel(const QrJob* __restrict__ jobs, double* __restrict__ ws,
                                                  const int* __restrict__ only, int* __restrict__ nrun) {
   if (only && !only[blockIdx.x]) return;  // masked launch: fallback sectors only
   if (nrun && threadIdx.x == 0) atomicAdd(nrun, 1);
-  const QrJob J = jobs[blockIdx.x];
+  qr_one(jobs[blockIdx.x], ws);
+}
+
+// one matrix whose job record travels as a kernel argument (no device copy of it)
+__global__ void __launch_bounds__(QRT) qr_byval_kernel(const QrJob J, double* __restrict__ ws) { qr_one(J, ws); }
+
+__device__ __forceinline__ void qr_one(const QrJob J, double* __restrict__ ws) {
   const int m = J.m, n = J.n;
   double* A = ws + J.a;
   double* Qm = ws + J.q;
@@ -926,6 +934,11 @@ cudaError_t launch_scale_rc(double* a, long long ld, int rows, int cols, const d
 cudaError_t launch_qr(const QrJob* jobs, int njobs, double* ws, cudaStream_t s) {
   if (njobs == 0) return cudaSuccess;
   qr_kernel<<<njobs, QRT, 0, s>>>(jobs, ws, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qr_job(const QrJob& job, double* ws, cudaStream_t s) {
+  qr_byval_kernel<<<1, QRT, 0, s>>>(job, ws);
   return cudaGetLastError();
 }
 

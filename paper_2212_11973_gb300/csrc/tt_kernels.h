@@ -61,6 +61,9 @@ struct RhoScalars {
 };
 
 cudaError_t launch_gemm_f64(const DevGemm& g, const Bases& b, cudaStream_t s);
+// Exact-accumulation split GEMM (tt_ozaki.cu): FP64 operands of the FP64
+// plans, four fixed-point BF16 digits per K tile, ~2^-32 normwise.
+cudaError_t launch_gemm_oz(const DevGemm& g, const Bases& b, cudaStream_t s);
 // nsplit = 2 (3 products) or 3 (6 products); operand level l at offset l * lo[slot]
 cudaError_t launch_gemm_bf16(const DevGemm& g, const Bases& b, int nsplit, cudaStream_t s);
 // in_type / out_type: 0 = double, 1 = float, 2 / 3 = split bf16 with that many levels
@@ -71,10 +74,18 @@ cudaError_t launch_zero(void* p, size_t bytes, cudaStream_t s);
 // strided FP64 -> split-bf16 copy (levels at dst + l * lo[slot(dst)])
 cudaError_t launch_split_copy(const DevCopy& c, const Bases& b, int nsplit, cudaStream_t s);
 // tcgen05 grouped GEMM (tt_tcgen05.cu): K-major A and B, 128 x 128 tiles,
-// maps = 2 CUtensorMap (A, B) per segment in global memory.
+// maps = 3 CUtensorMap per segment in global memory: A (box 64 K x 128 rows),
+// B (64 x 128), B (64 x 64).
 size_t tc_smem_bytes(int nsplit);
+// Persistent warp-specialised variant (tt_tcgen05p.cu): 128 x 64 tiles, one
+// CTA per SM, TMA ring / MMA warp / fold-and-epilogue warps, the same
+// arithmetic and maps.
+size_t tcp_smem_bytes(int nsplit);
+cudaError_t launch_gemm_tcp(const GGroup* groups, const GSeg* segs, const GTile* tiles128x64, int ntiles,
+                            const void* maps, const Bases& b, int nsplit, int* err, long long wait_ns, cudaStream_t s);
+// err: set to 1 by a CTA whose bounded wait (budget wait_ns) ran out.
 cudaError_t launch_gemm_tc(const GGroup* groups, const GSeg* segs, const GTile* tiles128, int ntiles,
-                           const void* maps, const Bases& b, int nsplit, int* err, cudaStream_t s);
+                           const void* maps, const Bases& b, int nsplit, int* err, long long wait_ns, cudaStream_t s);
 
 // Lanczos exponential steps on flat FP64 vectors of length n.  Q holds the
 // Krylov basis with leading dimension ldq.  `partial` is scratch of
@@ -97,6 +108,8 @@ cudaError_t k_normalise_inplace(double* v, int64_t n, double* partial, KrylovSta
 
 // Householder QR of a batch of column-major matrices in workspace `ws`.
 cudaError_t launch_qr(const QrJob* jobs, int njobs, double* ws, cudaStream_t s);
+// one job passed by value (the record is a kernel argument, not device memory)
+cudaError_t launch_qr_job(const QrJob& job, double* ws, cudaStream_t s);
 // the same, only for the jobs whose only[job] != 0
 // Householder QR of the jobs whose flag in `only` is set; *nrun (if not null)
 // counts the sectors factorised.

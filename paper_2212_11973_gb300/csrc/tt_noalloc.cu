@@ -8,10 +8,12 @@
 // a fixed array in device global memory that every GPU which loads this
 // library reserves for the life of the process.
 //
-// Scratch layout (doubles): [0, 8) the job record read by the kernel, then the
-// working copy of A (m*n), Q (m*n) and R (n*n).  The QR kernel writes every
-// element of Q and R and the working copy is filled from A before the kernel
-// runs, so nothing has to start at zero.
+// Scratch layout (doubles): the working copy of A (m*n), then Q (m*n) and R
+// (n*n).  The job record (offsets and sizes) is a kernel argument, so the call
+// queues no host-to-device copy: a copy from pageable host memory would make
+// the stream wait before staging it.  The QR kernel writes every element of Q
+// and R and the working copy is filled from A before the kernel runs, so
+// nothing has to start at zero.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -22,7 +24,6 @@
 namespace {
 
 constexpr size_t kScratchDoubles = size_t(1) << 21;  // 16 MiB per GPU
-constexpr size_t kJobDoubles = 8;                      // room for one QrJob (40 bytes)
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -50,7 +51,7 @@ double* scratch_address(int device) {
 extern "C" tt_status tt_qr_device_noalloc(const double* A, int m, int n, double* Q, double* R, void* cuda_stream) {
   if (!A || !Q || !R || m < 1 || n < 1 || n > 2048 || m < n) return TT_ERR_INVALID_ARG;
   const size_t mn = (size_t)m * (size_t)n;
-  if (kJobDoubles + 2 * mn + (size_t)n * n > kScratchDoubles) return TT_ERR_INVALID_ARG;  // beyond the fixed scratch
+  if (2 * mn + (size_t)n * n > kScratchDoubles) return TT_ERR_INVALID_ARG;  // beyond the fixed scratch
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -59,11 +60,10 @@ extern "C" tt_status tt_qr_device_noalloc(const double* A, int m, int n, double*
   double* s = scratch_address(dev);
   if (!s) return TT_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  double* ws = s + kJobDoubles;
+  double* ws = s;
   const tt::QrJob job{0, (int64_t)mn, (int64_t)(2 * mn), m, n};
-  if (cudaMemcpyAsync(s, &job, sizeof(job), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(ws, A, mn * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-      tt::launch_qr(reinterpret_cast<const tt::QrJob*>(s), 1, ws, st) != cudaSuccess ||
+  if (cudaMemcpyAsync(ws, A, mn * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+      tt::launch_qr_job(job, ws, st) != cudaSuccess ||
       cudaMemcpyAsync(Q, ws + mn, mn * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(R, ws + 2 * mn, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
     cudaGetLastError();

@@ -11,12 +11,18 @@
 // (TwoSum, Knuth TAOCP 4.2.2), so the FP32 accumulation error does not grow
 // with K.  The epilogue stages hi + lo through shared memory and writes FP32
 // or FP64 rows coalesced.  Two shared-memory stages overlap the TMA of chunk c+1 with the
-// MMAs of chunk c.  Every mbarrier wait is bounded: on expiry the CTA records
-// an error code, drains its own copies in flight, frees its TMEM and returns.
+// MMAs of chunk c.  Every mbarrier wait is bounded by a time budget (ns, a
+// kernel argument, measured on %globaltimer).  Thread 0 alone waits on the
+// copy, MMA and accumulator barriers and broadcasts an abort through shared
+// memory, so all threads leave the main loop together.  On abort the CTA
+// records an error code, waits (with a fixed drain budget) for the at most two
+// TMA chunks still in flight and for its last MMA commit, frees its TMEM and
+// returns.
 //
 // Both operands must be K-major (A stored M x K, B stored N x K, K contiguous)
 // with leading dimensions and offsets that are multiples of 8 elements; the
-// host checks this before choosing the kernel.
+// host checks this before choosing the kernel.  maps holds three tensor maps
+// per segment: A (box 64 K x 128 rows), B (64 x 128), B (64 x 64).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -24,10 +30,13 @@
 #include <cstdint>
 
 #include "tt_kernels.h"
+#include "tt_tc_ptx.h"
 
 namespace tt {
 
 namespace {
+
+using namespace tcx;
 
 constexpr int TBM = 128, TBN = 128, TBK = 64;
 constexpr int TILE_BYTES = TBM * TBK * 2;  // 16 KB per level and operand
@@ -39,115 +48,13 @@ constexpr int FOLD = 2;                    // chunks per TMEM fold
 // accumulation act on the dominant term only 4 times per 64-long K chunk
 // instead of 4 * (number of products) times.
 constexpr uint32_t TMEM_COLS = 512;
-constexpr long long WAIT_LIMIT = 1ll << 26;
-
-__device__ __forceinline__ int slot_of(Ref r) { return (int)(r >> 56); }
-__device__ __forceinline__ long long off_of(Ref r) { return (long long)(r & 0x00FFFFFFFFFFFFFFull); }
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(phase)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait; returns false when the limit expired
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
-  for (long long i = 0; i < WAIT_LIMIT; ++i)
-    if (mbar_try_wait(bar, phase)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (SBO), version 1 (sm_100 family).
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
-  d |= (uint64_t)1 << 46;               // descriptor version
-  d |= (uint64_t)2 << 61;               // SWIZZLE_128B
-  return d;
-}
-
-__device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
-      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
-      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
-      "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])),
-      "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])),
-      "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])),
-      "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])),
-      "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])),
-      "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])),
-      "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
-      : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 template <int NS>
 __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restrict__ groups,
                                                          const GSeg* __restrict__ segs,
                                                          const GTile* __restrict__ tiles,
                                                          const CUtensorMap* __restrict__ maps, Bases bs,
-                                                         int* __restrict__ err) {
+                                                         int* __restrict__ err, long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[2], empty_bar[2], acc_bar;
   __shared__ uint32_t tmem_base_s;
@@ -195,8 +102,8 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
     while (cur_seg < g.seg1 && cur_k >= segs[cur_seg].K) { ++cur_seg; cur_k = 0; }
     const int s = c & 1;
     uint8_t* st = smem + s * STAGE_BYTES;
-    const CUtensorMap* ma = maps + 2 * cur_seg;
-    const CUtensorMap* mb = maps + 2 * cur_seg + 1;
+    const CUtensorMap* ma = maps + 3 * cur_seg;
+    const CUtensorMap* mb = maps + 3 * cur_seg + 1;
     if (fenced_seg != cur_seg) {  // tensor maps written by a host copy: acquire before first use
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma)) : "memory");
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb)) : "memory");
@@ -210,7 +117,13 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
     cur_k += TBK;
   };
 
-  int issued = 0;   // TMA chunks issued
+  // Thread 0's bookkeeping for a clean abort: chunks [consumed, issued) may
+  // still have TMA copies in flight; last_commit is the last chunk whose MMAs
+  // were committed to its empty barrier (they complete in issue order, so that
+  // commit covers every earlier MMA); acc_pending marks an accumulator commit
+  // whose wait did not succeed.
+  int issued = 0, consumed = 0, last_commit = -1;
+  bool acc_pending = false;
   int folds = 0;
   bool ok = true;
   float v[32], u[32], h[32], w[32];
@@ -220,13 +133,15 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
       for (int c = b0; c < b1 && ok; ++c) {
         if (issued == c) { issue_tma(c); ++issued; }
         if (c + 1 < total && issued == c + 1) {
-          if (c + 1 >= 2) ok = ok && mbar_wait(&empty_bar[(c + 1) & 1], ((c - 1) >> 1) & 1);
+          // stage (c+1)&1 was last read by the MMAs of chunk c-1
+          if (c + 1 >= 2) ok = mbar_wait(&empty_bar[(c + 1) & 1], ((c - 1) >> 1) & 1, wait_ns);
           if (ok) { issue_tma(c + 1); ++issued; }
         }
         if (!ok) break;
         const int s = c & 1;
-        ok = mbar_wait(&full_bar[s], (c >> 1) & 1);
+        ok = mbar_wait(&full_bar[s], (c >> 1) & 1, wait_ns);
         if (!ok) break;
+        consumed = c + 1;
         fence_after();
         const uint32_t sa = smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
@@ -241,16 +156,18 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
           }
         }
         umma_commit(&empty_bar[s]);
+        last_commit = c;
       }
-      if (ok) umma_commit(&acc_bar);
-      else abort_s = 1;
+      if (ok) {
+        umma_commit(&acc_bar);
+        acc_pending = true;
+        ok = mbar_wait(&acc_bar, folds & 1, wait_ns);
+        if (ok) acc_pending = false;
+      }
+      abort_s = ok ? 0 : 1;
     }
     __syncthreads();
     if (abort_s) break;
-    if (!mbar_wait(&acc_bar, folds & 1)) {
-      abort_s = 1;
-      break;
-    }
     fence_after();
 #pragma unroll 1
     for (int cb = 0; cb < TBN; cb += 32) {
@@ -282,10 +199,14 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
   }
 
   if (abort_s) {
-    // drain the copies this CTA may still have in flight, then give up
+    // drain what this CTA still has in flight, then give up: the TMA chunks
+    // not yet consumed (at most two, each the newest phase of its barrier),
+    // the MMAs up to the last commit, and an unconsumed accumulator commit
     if (tid == 0) {
       if (err) atomicExch(err, 1);
-      for (int c = 0; c < issued; ++c) mbar_wait(&full_bar[c & 1], (c >> 1) & 1);
+      for (int c = consumed; c < issued; ++c) mbar_wait(&full_bar[c & 1], (c >> 1) & 1, DRAIN_NS);
+      if (last_commit >= 0) mbar_wait(&empty_bar[last_commit & 1], (last_commit >> 1) & 1, DRAIN_NS);
+      if (acc_pending) mbar_wait(&acc_bar, folds & 1, DRAIN_NS);
     }
     __syncthreads();
   } else {
@@ -344,7 +265,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
 size_t tc_smem_bytes(int nsplit) { return (size_t)2 * 2 * nsplit * TILE_BYTES + 1024; }
 
 cudaError_t launch_gemm_tc(const GGroup* groups, const GSeg* segs, const GTile* tiles128, int ntiles,
-                           const void* maps, const Bases& b, int nsplit, int* err, cudaStream_t s) {
+                           const void* maps, const Bases& b, int nsplit, int* err, long long wait_ns, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   const size_t smem = tc_smem_bytes(nsplit);
   if (nsplit == 2) {
@@ -352,13 +273,13 @@ cudaError_t launch_gemm_tc(const GGroup* groups, const GSeg* segs, const GTile* 
     static const cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)smem);
     if (e != cudaSuccess) return e;
-    gemm_tc_kernel<2><<<ntiles, 128, smem, s>>>(groups, segs, tiles128, (const CUtensorMap*)maps, b, err);
+    gemm_tc_kernel<2><<<ntiles, 128, smem, s>>>(groups, segs, tiles128, (const CUtensorMap*)maps, b, err, wait_ns);
   } else if (nsplit == 3) {
     // once per process (thread-safe static initialisation)
     static const cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                       (int)smem);
     if (e != cudaSuccess) return e;
-    gemm_tc_kernel<3><<<ntiles, 128, smem, s>>>(groups, segs, tiles128, (const CUtensorMap*)maps, b, err);
+    gemm_tc_kernel<3><<<ntiles, 128, smem, s>>>(groups, segs, tiles128, (const CUtensorMap*)maps, b, err, wait_ns);
   } else {
     return cudaErrorInvalidValue;
   }

@@ -43,7 +43,8 @@ class tt_model(C.Structure):
 
 class tt_run_opts(C.Structure):
     _fields_ = [("D_max", C.c_int), ("krylov_dim", C.c_int), ("precision", C.c_int),
-                ("growth_precision", C.c_int), ("svd_cut", C.c_double), ("degen_tol", C.c_double)]
+                ("growth_precision", C.c_int), ("svd_cut", C.c_double), ("degen_tol", C.c_double),
+                ("env_precision", C.c_int)]
 
 
 class tt_obs(C.Structure):
@@ -63,7 +64,8 @@ class tt_stats(C.Structure):
                 ("n_sites", C.c_int), ("max_bond", C.c_int), ("n_sectors_max", C.c_int),
                 ("qr_ms", C.c_double), ("bond_flops", C.c_double), ("qr_sectors", C.c_longlong), ("qr_fallbacks", C.c_longlong),
                 ("site_exp_ms", C.c_double), ("bond_exp_ms", C.c_double), ("env_update_ms", C.c_double),
-                ("absorb_ms", C.c_double), ("gauge_ms", C.c_double)]
+                ("absorb_ms", C.c_double), ("gauge_ms", C.c_double),
+                ("tuned_tc128", C.c_longlong), ("tuned_tcp128x64", C.c_longlong), ("tuned_mma64", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -78,6 +80,7 @@ SIGNATURES = {
     "tt_ctx_create": (C.c_int, [C.POINTER(tt_alloc_cb), _P, C.POINTER(_P)]),
     "tt_ctx_destroy": (None, [_P]),
     "tt_last_error": (C.c_char_p, [_P]),
+    "tt_ctx_set_wait_limit": (C.c_int, [_P, C.c_double]),
     "tt_hubbard_mpo_create": (C.c_int, [_P, C.POINTER(tt_model), C.POINTER(_P)]),
     "tt_mpo_destroy": (None, [_P]),
     "tt_mpo_num_sites": (C.c_int, [_P]),
@@ -86,6 +89,7 @@ SIGNATURES = {
     "tt_rho_create": (C.c_int, [_P, _P, C.c_double, C.c_int, C.POINTER(tt_run_opts), C.POINTER(_P)]),
     "tt_rho_destroy": (None, [_P]),
     "tt_rho_grow": (C.c_int, [_P, _P, C.c_double, C.c_double, _PD]),
+    "tt_rho_grow_exp": (C.c_int, [_P, _P, C.c_double, C.c_double, _PD]),
     "tt_tdvp_step": (C.c_int, [_P, _P, C.c_double, C.c_int]),
     "tt_rho_pad": (C.c_int, [_P, _P, C.c_int]),
     "tt_measure": (C.c_int, [_P, _P, C.POINTER(tt_obs)]),
@@ -97,6 +101,9 @@ SIGNATURES = {
     "tt_rho_load": (C.c_int, [_P, _P, C.c_char_p, C.POINTER(tt_run_opts), C.POINTER(_P)]),
     "tt_layout_sizes": (C.c_int, [_P, C.c_int, _PI, _PI, _PI, _PI, _PL, _PL, _PL]),
     "tt_heff_apply_host": (C.c_int, [_P, _P, C.c_int, C.c_int, _PI, _PI, _PI, _PI, _PD, _PD, _PD, _PD]),
+    "tt_heff_apply_terms_host": (C.c_int, [_P, C.c_int, _PI, _PI, C.c_int, _PI, _PI, C.c_int, _PI, _PI, _PI, _PI,
+                                           _PD, C.c_int, _PI, _PI, _PI, _PI, _PD, _PD, _PD, _PD]),
+    "tt_layout_sizes_terms": (C.c_int, [C.c_int, _PI, _PI, C.c_int, _PI, _PI, _PI, _PI, _PI, _PI, _PL, _PL, _PL]),
     "tt_qr_device": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
     "tt_qr_device_noalloc": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "tt_batch_create": (C.c_int, [_P, C.c_int, C.POINTER(tt_model), _PI, C.c_double, C.POINTER(tt_run_opts),
@@ -170,6 +177,9 @@ class Context:
             raise TTError(st, "tt_ctx_create failed")
         self.h = h
 
+    def set_wait_limit(self, seconds: float):
+        _check(self.h, load_library().tt_ctx_set_wait_limit(self.h, float(seconds)))
+
     def close(self):
         if getattr(self, "h", None):
             load_library().tt_ctx_destroy(self.h)
@@ -216,17 +226,18 @@ class Mpo:
             pass
 
 
-def run_opts(D_max, krylov_dim=8, precision=TT_PREC_FP64, growth_precision=-1, svd_cut=1e-12, degen_tol=1e-10):
-    return tt_run_opts(D_max, krylov_dim, precision, growth_precision, svd_cut, degen_tol)
+def run_opts(D_max, krylov_dim=8, precision=TT_PREC_FP64, growth_precision=-1, svd_cut=1e-12, degen_tol=1e-10,
+             env_precision=0):
+    return tt_run_opts(D_max, krylov_dim, precision, growth_precision, svd_cut, degen_tol, env_precision)
 
 
 class Rho:
-    def __init__(self, ctx: Context, mpo: Mpo, beta0: float, opts: tt_run_opts, handle=None):
+    def __init__(self, ctx: Context, mpo: Mpo, beta0: float, opts: tt_run_opts, handle=None, taylor_order: int = 1):
         lib = load_library()
         self.ctx, self.mpo, self.opts = ctx, mpo, opts
         if handle is None:
             h = C.c_void_p()
-            _check(ctx.h, lib.tt_rho_create(ctx.h, mpo.h, beta0, 1, C.byref(opts), C.byref(h)))
+            _check(ctx.h, lib.tt_rho_create(ctx.h, mpo.h, beta0, taylor_order, C.byref(opts), C.byref(h)))
             handle = h
         self.h = handle
 
@@ -239,6 +250,11 @@ class Rho:
     def grow(self, dtau, beta_max):
         b = C.c_double()
         _check(self.ctx.h, load_library().tt_rho_grow(self.h, self.mpo.h, dtau, beta_max, C.byref(b)))
+        return b.value
+
+    def grow_exp(self, ratio, beta_max):
+        b = C.c_double()
+        _check(self.ctx.h, load_library().tt_rho_grow_exp(self.h, self.mpo.h, ratio, beta_max, C.byref(b)))
         return b.value
 
     def pad(self, D_target):
@@ -322,6 +338,51 @@ def heff_apply_host(ctx: Context, mpo: Mpo, site, precision, sectors_l, sectors_
     pd = lambda a: a.ctypes.data_as(_PD)  # noqa: E731
     _check(ctx.h, load_library().tt_heff_apply_host(ctx.h, mpo.h, site, precision, nsec, qn, qs, qd,
                                                      pd(L), pd(R), pd(x), pd(y)))
+    return y
+
+
+def _terms_args(chl, chr_, terms):
+    import numpy as np
+    t = list(terms)
+    return (len(chl), _int_array([c[0] for c in chl]), _int_array([c[1] for c in chl]),
+            len(chr_), _int_array([c[0] for c in chr_]), _int_array([c[1] for c in chr_]),
+            len(t), _int_array([x[0] for x in t]), _int_array([x[1] for x in t]), _int_array([x[2] for x in t]),
+            _int_array([x[3] for x in t]), np.ascontiguousarray([x[4] for x in t], dtype=np.float64))
+
+
+def layout_sizes_terms(chl, chr_, sectors_l, sectors_r):
+    """Element counts (x, L, R) for MPO channels chl / chr_ (lists of (n, 2Sz))."""
+    secs = list(sectors_l) + list(sectors_r)
+    nsec = _int_array([len(sectors_l), len(sectors_r)])
+    qn = _int_array([s[0] for s in secs])
+    qs = _int_array([s[1] for s in secs])
+    qd = _int_array([s[2] for s in secs])
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    nl, cln, cls, nr, crn, crs = _terms_args(chl, chr_, [])[:6]
+    st = load_library().tt_layout_sizes_terms(nl, cln, cls, nr, crn, crs, nsec, qn, qs, qd,
+                                              C.byref(a), C.byref(b), C.byref(c))
+    _check(None, st)
+    return a.value, b.value, c.value
+
+
+def heff_apply_terms_host(ctx: Context, chl, chr_, terms, precision, sectors_l, sectors_r, L, R, x):
+    """One H^(1) apply with a caller-supplied MPO tensor: terms are
+    (wl, wr, sig, tau, value) with <sig|op|tau>; chl / chr_ the channel charges."""
+    import numpy as np
+    secs = list(sectors_l) + list(sectors_r)
+    nsec = _int_array([len(sectors_l), len(sectors_r)])
+    qn = _int_array([s[0] for s in secs])
+    qs = _int_array([s[1] for s in secs])
+    qd = _int_array([s[2] for s in secs])
+    nl, cln, cls, nr, crn, crs, nt, twl, twr, tsg, tta, tv = _terms_args(chl, chr_, terms)
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    pd = lambda a: a.ctypes.data_as(_PD)  # noqa: E731
+    _check(ctx.h, load_library().tt_heff_apply_terms_host(ctx.h, nl, cln, cls, nr, crn, crs, nt, twl, twr, tsg, tta,
+                                                           pd(tv), precision, nsec, qn, qs, qd,
+                                                           pd(L), pd(R), pd(x), pd(y)))
     return y
 
 

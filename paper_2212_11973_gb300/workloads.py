@@ -36,10 +36,13 @@ class Workload:
         return self.Lx * self.Wy
 
 
-# Chemical potential for about 1/8 hole doping at U = 8 in the particle-hole
-# symmetric form (n = 7/8 at beta = 10).  Provisional: the FP64 D = 128 CL4x8
-# bisection bracketed it in [-3.5, -1.52] (n = 0.632 and 0.99995 there).
-MU_EIGHTH_DOPING = -2.0
+# Chemical potential for 1/8 hole doping at U = 8 in the particle-hole
+# symmetric form: n = 7/8 at beta = 10 on CL4x8 (FP64, D = 128, growth to
+# beta = 1 then 1-TDVP steps of 0.05).  Measured n(mu): -2.4: 0.9038,
+# -2.45: 0.8861, -2.5: 0.8693, -2.55: 0.8532, -2.7: 0.8087, -3.0: 0.7325;
+# linear interpolation between -2.45 and -2.5 puts n = 7/8 at -2.483, frozen
+# at -2.48 (n = 0.876 interpolated, inside 7/8 +- 0.005).
+MU_EIGHTH_DOPING = -2.48
 
 CLUSTER_2x2 = Workload("2x2 open cluster U=4 mu=0 D=64", 2, 2, False, 1.0, 4.0, 0.0, 1, 64, 0.01, 0.05, 4.0)
 CLUSTER_2x2_FULL = replace(CLUSTER_2x2, name="2x2 open cluster U=4 mu=0 untruncated D=256", D=256)

@@ -100,6 +100,41 @@ def test_full_rank_two_site_growth_is_exact():
         assert _rel(ob[k], ed[k]) < 1e-10, (k, ob[k], ed[k])
 
 
+def test_two_site_growth_on_exponential_grid_is_exact():
+    """2-TDVP steps along beta_n = 2^(n/4) beta_0 (Fig. S7(b) grids) on the
+    padded state: exact at full rank like the linear grid."""
+    m = om.Model(1, 3, False, U=3.0, mu=0.4, form=0)
+    st = tt.pad_to_full_rank(tt.init_state(ompo.hubbard_mpo(m), 0.01))
+    r = 2.0 ** 0.25
+    betas = []
+    while st.beta < 0.3 - 1e-12:
+        tt.tdvp2_step(st, min(st.beta * (r - 1.0), 0.3 - st.beta), tt.TruncOpts(16, svd_cut=0.0))
+        betas.append(st.beta)
+    assert len(betas) == math.ceil(math.log(0.3 / 0.01) / math.log(r))
+    ob = tt.measure(st)
+    ed = om.ed_thermo(m, [st.beta], beta0=0.01)[0]
+    for k in KEYS:
+        assert _rel(ob[k], ed[k]) < 1e-10, (k, ob[k], ed[k])
+
+
+def test_run_follows_the_exponential_growth_grid():
+    """run(grow_ratio=r): growth steps beta -> r beta, the last one ending at
+    grow_until, then linear steps of dtau."""
+    m = om.Model(2, 2, False, U=4.0, mu=0.0, form=1)
+    rec = []
+    r = 2.0 ** 0.5
+    tt.run(ompo.hubbard_mpo(m), 0.01, 0.05, 0.25, tt.TruncOpts(8), grow_until=0.15, grow_ratio=r,
+           callback=lambda st, stage: rec.append((st.beta, stage)))
+    grow = [b for b, s in rec if s == "grow"]
+    lin = [b for b, s in rec if s == "tdvp1"]
+    want, b = [], 0.01
+    while b < 0.15 - 1e-12:
+        b = min(b * r, 0.15)
+        want.append(b)
+    assert np.allclose(grow, want, rtol=0, atol=1e-14)
+    assert np.allclose(np.diff([grow[-1]] + lin), 0.05, rtol=0, atol=1e-14)
+
+
 def test_compact_initial_state():
     """The compact rho_0 has the operator Schmidt ranks of I - beta0 H/2:
     2 + 4 x (distinct left ends of hopping bonds crossing the cut), minus
@@ -302,3 +337,48 @@ def test_symmetric_sweep_is_second_order_in_dtau():
     e = [abs(f[dt] - f[0.00625]) for dt in (0.2, 0.1, 0.05, 0.025)]
     slopes = [math.log2(e[i] / e[i + 1]) for i in range(3)]
     assert all(1.8 < s < 2.3 for s in slopes), slopes
+
+
+def test_series_initial_state_order_one_is_the_first_order_state():
+    """init_state_series(order=1) (dense, SVD cut) and init_state (from the
+    MPO, compressed) are the same operator I - beta0 H/2: equal observables."""
+    m = om.Model(2, 2, False, U=4.0, mu=-0.3, form=1)
+    W = ompo.hubbard_mpo(m)
+    a, b = tt.init_state(W, 0.05), tt.init_state_series(W, 0.05, 1)
+    assert a.bond_dims() == b.bond_dims()
+    oa, ob = tt.measure(a), tt.measure(b)
+    for k in KEYS:
+        assert _rel(oa[k], ob[k]) < 1e-13, (k, oa[k], ob[k])
+
+
+def test_series_initial_state_evolves_exactly_at_full_rank():
+    """Third-order series state padded to maximal bonds: 1-TDVP reproduces ED
+    of exp(-(beta-beta0) H/2) sum_{k<=3} (-beta0 H/2)^k/k! (exactness on the
+    whole space)."""
+    m = om.Model(1, 3, False, U=3.0, mu=0.4, form=0)
+    W = ompo.hubbard_mpo(m)
+    st = tt.run(W, 0.05, 0.05, 0.46, tt.TruncOpts(16), pad_full=True, taylor_order=3)
+    ob = tt.measure(st)
+    ed = om.ed_thermo(m, [st.beta], beta0=0.05, order=3)[0]
+    for k in KEYS:
+        assert _rel(ob[k], ed[k]) < 1e-10, (k, ob[k], ed[k])
+    ed1 = om.ed_thermo(m, [st.beta], beta0=0.05, order=1)[0]
+    assert _rel(ed1["lnZ"], ed["lnZ"]) > 1e-6  # the order matters at this beta0
+
+
+def test_series_initial_state_converges_to_the_gibbs_state():
+    """ln Z of the order-n state at beta0 approaches the exact exp(-beta0 H)
+    value; the error falls by about beta0 ||H|| per order (SETTN removes the
+    expansion error, Fig. S7(a))."""
+    m = om.Model(1, 3, False, U=4.0, mu=-0.3, form=1)
+    W = ompo.hubbard_mpo(m)
+    beta0 = 0.02
+    exact = om.ed_thermo(m, [beta0], beta0=0.0)[0]["lnZ"]
+    errs = []
+    for order in (1, 2, 3, 4, 6):
+        st = tt.init_state_series(W, beta0, order)
+        errs.append(abs(tt.measure(st)["lnZ"] - exact))
+        ed = om.ed_thermo(m, [beta0], beta0=beta0, order=order)[0]["lnZ"]
+        assert abs(tt.measure(st)["lnZ"] - ed) < 1e-12 * abs(ed)
+    assert errs[1] < 0.2 * errs[0] and errs[2] < 0.2 * errs[1] and errs[3] < 0.2 * errs[2]
+    assert errs[4] < 1e-12 * abs(exact)
