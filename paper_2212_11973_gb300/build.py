@@ -15,7 +15,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libtantrg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tt_model.cpp", "tt_plans.cpp", "tt_kernels.cu", "tt_tcgen05.cu", "tt_tcgen05p.cu", "tt_ozaki.cu", "tt_engine.cu", "tt_batch.cu", "tt_noalloc.cu"]
+SOURCES = ["tt_model.cpp", "tt_plans.cpp", "tt_kernels.cu", "tt_tcgen05.cu", "tt_tcgen05p.cu", "tt_tcgen05z.cu", "tt_digits.cu", "tt_ozaki.cu", "tt_engine.cu", "tt_batch.cu", "tt_noalloc.cu"]
 
 
 def _nvcc() -> str:

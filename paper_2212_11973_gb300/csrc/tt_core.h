@@ -153,6 +153,10 @@ struct GSeg {
   Ref A, B;
   int lda, ldb, K;
   int tA, tB;  // tA: A stored K x M (row-major) ; tB: B stored N x K (row-major)
+  // fixed-point digit operands (exact-accumulation split): the int16 row
+  // exponents of A (row m at eA + m * eas) and of B (row n at eB + n * ebs)
+  Ref eA = 0, eB = 0;
+  int eas = 0, ebs = 0;
 };
 struct GTile {
   int g, m0, n0, pad;
@@ -170,6 +174,14 @@ struct GemmPlan {
     g.seg1 = (int)segs.size();
     flops += 2.0 * g.M * (double)g.N * K;
   }
+  // row exponents of the last segment's digit operands
+  void set_exps(Ref eA, int eas, Ref eB, int ebs) {
+    GSeg& s = segs.back();
+    s.eA = eA;
+    s.eas = eas;
+    s.eB = eB;
+    s.ebs = ebs;
+  }
 };
 
 struct GItem {
@@ -177,6 +189,9 @@ struct GItem {
   int64_t dst_rs;
   int rows, cols;
   int c0, c1;
+  // digit output: the int16 exponent of item row i at e + i * e_rs
+  Ref e = 0;
+  int64_t e_rs = 0;
 };
 struct GContrib {
   Ref src;
@@ -197,6 +212,19 @@ struct CItem {
 // FP64 -> split-bf16 copy (levels at dst + l * lo[slot(dst)]) uses CItem too.
 struct CopyPlan {
   std::vector<CItem> items;
+};
+
+// FP64 rows -> fixed-point BF16 digit rows (exact-accumulation split): row r
+// has cols values at src + r * s_r + k * s_k; digit level l of element k goes
+// to dst + r * dst_rs + k + l * lo[slot(dst)], the row's int16 exponent to
+// e + r * e_rs.
+struct DItem {
+  Ref src, dst, e;
+  int64_t s_r, s_k, dst_rs, e_rs;
+  int rows, cols;
+};
+struct DigitPlan {
+  std::vector<DItem> items;
 };
 
 // QR job: column-major m x n matrix at ws offset `a` (ld = m); Q written to `q`

@@ -160,6 +160,17 @@ void release(tt_ctx* c, DevGemmBuf& o) {
 void release(tt_ctx* c, DevGatherBuf& o) { dfree(c, o.buf); o.d = DevGather(); o.host = GatherPlan(); o.checked = false; }
 void release(tt_ctx* c, DevCopyBuf& o) { dfree(c, o.buf); o.d = DevCopy(); o.host = CopyPlan(); o.checked = false; }
 
+void upload(tt_ctx* c, const DigitPlan& p, DevDigitBuf& o) {
+  ensure(c, o.buf, p.items.size() * sizeof(DItem) + 16);
+  if (!p.items.empty())
+    CK(cudaMemcpyAsync(o.buf.p, p.items.data(), p.items.size() * sizeof(DItem), cudaMemcpyHostToDevice, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  o.d.items = (DItem*)o.buf.p;
+  o.d.nitems = (int)p.items.size();
+  o.host = p;
+}
+void release(tt_ctx* c, DevDigitBuf& o) { dfree(c, o.buf); o.d = DevDigit(); o.host = DigitPlan(); }
+
 static void check_ref(Ref r, int64_t last, const Caps& c, const char* what, const char* op) {
   int slot = (int)(r >> 56);
   int64_t off = (int64_t)(r & 0x00FFFFFFFFFFFFFFull);
@@ -186,6 +197,35 @@ void check_plan(const GemmPlan& p, const Caps& c, const char* what) {
       check_ref(s.A, alast, c, what, "A");
       check_ref(s.B, blast, c, what, "B");
     }
+  }
+}
+
+// digit exponents of a GEMM plan: ex = capacity per slot of the exponent
+// region (which starts after the four levels, i.e. at 4 * level size)
+void check_exps(const GemmPlan& p, const Caps& ex, const char* what) {
+  for (const GGroup& g : p.groups) {
+    if (g.M <= 0 || g.N <= 0) continue;
+    for (int si = g.seg0; si < g.seg1; ++si) {
+      const GSeg& s = p.segs[si];
+      if (s.K <= 0) continue;
+      if (s.eas <= 0 || s.ebs <= 0) throw Err{TT_ERR_STATE, std::string("missing digit exponents in ") + what};
+      const int64_t ao = (int64_t)(s.eA & 0x00FFFFFFFFFFFFFFull), bo = (int64_t)(s.eB & 0x00FFFFFFFFFFFFFFull);
+      check_ref(s.eA, ao + (int64_t)(g.M - 1) * s.eas, ex, what, "exponents of A");
+      check_ref(s.eB, bo + (int64_t)(g.N - 1) * s.ebs, ex, what, "exponents of B");
+    }
+  }
+}
+
+void check_plan(const DigitPlan& p, const Caps& c, const Caps& ex, const char* what) {
+  for (const DItem& it : p.items) {
+    if (it.rows <= 0 || it.cols <= 0) continue;
+    const int64_t so = (int64_t)(it.src & 0x00FFFFFFFFFFFFFFull), d = (int64_t)(it.dst & 0x00FFFFFFFFFFFFFFull),
+                  eo = (int64_t)(it.e & 0x00FFFFFFFFFFFFFFull);
+    check_ref(it.src, so + (int64_t)(it.rows - 1) * it.s_r + (int64_t)(it.cols - 1) * it.s_k, c, what, "src");
+    check_ref(it.dst, d + (int64_t)(it.rows - 1) * it.dst_rs + it.cols - 1, c, what, "dst");
+    check_ref(it.e, eo + (int64_t)(it.rows - 1) * it.e_rs, ex, what, "exponents");
+    if (it.cols > tcz_max_k()) throw Err{TT_ERR_INVALID_ARG, std::string("exact split: a digit row longer than ") +
+                                                               std::to_string(tcz_max_k()) + " in " + what};
   }
 }
 
@@ -272,15 +312,15 @@ struct Eng {
   // invalidates the precision-dependent plans and re-splits the environments
   // that are valid with the centre on site 0 (L[0], R[1..N]).
   void set_precision(int prec) {
-    const int ns = (prec == 1) ? 2 : (prec == 2 ? 3 : 0);
-    const bool oz = prec == 3;
-    if (ns == r->nsplit && oz == r->oz_all) return;
+    const int ns = (prec == 1) ? 2 : (prec == 2 ? 3 : (prec == 3 ? 4 : 0));
+    const bool ex = prec == 3;
+    if (ns == r->nsplit && ex == r->exact) return;
     drop_graph();
-    r->oz_all = oz;
-    if (ns == r->nsplit) return;
+    r->exact = ex;
     r->nsplit = ns;
     for (auto& sp : r->sp) sp.valid = false;
     for (auto& bp : r->bp) bp.valid = false;
+    for (auto& e : r->esplit_ok) e = 0;
     if (ns == 0) return;
     const int N = r->N;
     if (r->L[0].p) { ensure_env(r->L, r->Lsp, r->Lsize, 0); split_env(r->L, r->Lsp, r->Lsize, 0); }
@@ -298,7 +338,7 @@ struct Eng {
       ensure(c, r->Qk, (size_t)cap * r->opts.krylov_dim * sizeof(double));
       ensure(c, r->W, (size_t)cap * sizeof(double));
       ensure(c, r->tmp, (size_t)cap * sizeof(double));
-      ensure(c, r->Xn, (size_t)cap * 3 * 2);
+      ensure(c, r->Xn, (size_t)cap * 4 * 2);
     }
   }
 
@@ -326,20 +366,23 @@ struct Eng {
     return s;
   }
   // environment updates in split-BF16 (else FP64 plans, also in mixed mode)
-  bool env_mixed() const { return mixed() && r->opts.env_precision == -1; }
+  bool env_mixed() const { return mixed() && !r->exact && r->opts.env_precision == -1; }
   // FP64 environment plans on the exact-accumulation split kernel
-  bool env_oz() const {
-    if (r->oz_all) return r->opts.env_precision != 1;
-    return mixed() && r->opts.env_precision == 0;
-  }
+  // (tt_ozaki.cu): the default in every split mode
+  bool env_oz() const { return mixed() && !env_mixed() && r->opts.env_precision != 1; }
+  // bytes per element of a split slot (levels, plus the int16 row exponents
+  // of the digit layouts, never more rows than elements)
+  size_t split_bytes() const { return (size_t)2 * (r->nsplit + (r->exact ? 1 : 0)); }
   SiteDev& site_plan(int j) {
     SiteDev& s = r->sp[j];
     if (s.valid) return s;
     const Mpo& m = M();
-    s.h = build_site_plan(r->bond[j], r->bond[j + 1], m.ls, m.site[j].terms, m.chan[j], m.chan[j + 1], mixed());
-    validate_site(s.h, r->bond[j], r->bond[j + 1], m.chan[j], m.chan[j + 1], mixed());
+    s.h = build_site_plan(r->bond[j], r->bond[j + 1], m.ls, m.site[j].terms, m.chan[j], m.chan[j + 1], mixed(),
+                          r->exact);
+    validate_site(s.h, r->bond[j], r->bond[j + 1], m.chan[j], m.chan[j + 1], mixed(), r->exact);
     upload(c, s.h.xsplit, s.xs);
-    if (mixed()) ensure(c, r->Xs, (size_t)std::max<int64_t>(s.h.xt_size, 1) * 2 * r->nsplit);
+    upload(c, s.h.xdig, s.xd);
+    if (mixed()) ensure(c, r->Xs, (size_t)std::max<int64_t>(s.h.xt_size, 1) * split_bytes());
     upload(c, s.h.s1, s.s1);
     upload(c, s.h.s2, s.s2);
     upload(c, s.h.s3, s.s3);
@@ -347,16 +390,15 @@ struct Eng {
     upload(c, s.h.r1, s.r1);
     upload(c, s.h.r2, s.r2);
     upload(c, s.h.r3, s.r3);
-    size_t el = mixed() ? 4 : 8;
     ensure(c, r->T1, (size_t)std::max(s.h.t1_size, s.h.u1_size) * 8);
-    ensure(c, r->T2, (size_t)std::max(s.h.t2_size, s.h.u2_size) * 8);  // FP64 or split levels
-    (void)el;
+    // FP64, split levels or digit levels plus exponents
+    ensure(c, r->T2, (size_t)std::max(s.h.t2_size, s.h.u2_size) * std::max<size_t>(8, split_bytes()));
     s.valid = true;
     return s;
   }
 
   static void validate_site(const SitePlanHost& h, const Bond& BL, const Bond& BR, const std::vector<Q>& chl,
-                            const std::vector<Q>& chr, bool mx) {
+                            const std::vector<Q>& chr, bool mx, bool ex = false) {
     const int64_t n = h.lay.size, el = make_env_layout(BL, chl).size, er = make_env_layout(BR, chr).size;
     const int64_t elo = make_env_layout(BL, chl, mx).size, ero = make_env_layout(BR, chr, mx).size;
     const int sx = mx ? S_AUX : S_X;  // natural-layout x operand
@@ -368,12 +410,32 @@ struct Eng {
     check_plan(h.r2, caps({{S_T1, h.u1_size}, {S_T2, h.u2_size}}), "R2");
     check_plan(h.r3, caps({{sx, n}, {S_T2, h.u2_size}, {S_Y, el}}), "R3");
     if (mx) check_plan(h.xsplit, caps({{S_X, n}, {S_Y, h.xt_size}}), "x split");
+    if (ex) {
+      // exponent regions: after the four levels, one int16 per digit row
+      const EnvLayout ELo = make_env_layout(BL, chl, true), ERo = make_env_layout(BR, chr, true);
+      int64_t lrows = 0, rrows = 0, xrows = 0, t2e = 0;
+      for (int64_t q : ELo.rows) lrows += q;
+      for (int64_t q : ERo.rows) rrows += q;
+      for (const SiteBlock& b : h.lay.blk) xrows += (int64_t)b.m * b.dr;
+      for (const GItem& it : h.s2.items) t2e = std::max<int64_t>(t2e, (int64_t)(it.e & 0x00FFFFFFFFFFFFFFull) +
+                                                                           (int64_t)(it.rows - 1) * it.e_rs + 1);
+      const Caps ex1 = caps({{S_L, 4 * elo + lrows}, {S_X, 4 * h.xt_size + xrows}});
+      const Caps ex3 = caps({{S_T2, std::max<int64_t>(t2e, 4 * h.t2_size + 1)}, {S_R, 4 * ero + rrows}});
+      check_exps(h.s1, ex1, "S1 exponents");
+      check_exps(h.s3, ex3, "S3 exponents");
+      check_plan(h.xdig, caps({{S_X, n}, {S_Y, h.xt_size}}), caps({{S_Y, 4 * h.xt_size + xrows}}), "x digits");
+      check_plan(h.s2, caps({{S_T1, h.t1_size}, {S_T2, h.t2_size}}), "S2");
+      if (t2e > 4 * h.t2_size + h.t2_size) throw Err{TT_ERR_STATE, "T2 exponents exceed the slot"};
+      for (const GItem& it : h.s2.items)
+        if (it.cols > gather_digits_max_cols())
+          throw Err{TT_ERR_INVALID_ARG, "exact split: a sector longer than " + std::to_string(gather_digits_max_cols())};
+    }
   }
 
   BondDev& bond_plan(int k) {
     BondDev& b = r->bp[k];
     if (b.valid) return b;
-    b.h = build_bond_plan(r->bond[k], M().chan[k], mixed());
+    b.h = build_bond_plan(r->bond[k], M().chan[k], mixed(), r->exact);
     {
       int64_t e = make_env_layout(r->bond[k], M().chan[k], mixed()).size;
       const int64_t xcap = mixed() ? b.h.xt_size : b.h.mat.size, tcap = mixed() ? b.h.tp_size : b.h.t_size;
@@ -383,14 +445,28 @@ struct Eng {
         check_plan(b.h.xsplit, caps({{S_X, b.h.mat.size}, {S_Y, b.h.xt_size}}), "B x split");
         check_plan(b.h.tsplit, caps({{S_T1, b.h.t_size}, {S_Y, b.h.tp_size}}), "B T split");
       }
+      if (r->exact) {
+        int64_t erows = 0, xrows = 0, trows = 0;
+        for (int64_t q : make_env_layout(r->bond[k], M().chan[k], true).rows) erows += q;
+        for (int d : r->bond[k].dim) xrows += d;
+        for (const DItem& it : b.h.tdig.items) trows += it.rows;
+        check_exps(b.h.b1, caps({{S_L, 4 * e + erows}, {S_X, 4 * b.h.xt_size + xrows}}), "B1 exponents");
+        check_exps(b.h.b2, caps({{S_T2, 4 * b.h.tp_size + trows}, {S_R, 4 * e + erows}}), "B2 exponents");
+        check_plan(b.h.xdig, caps({{S_X, b.h.mat.size}, {S_Y, b.h.xt_size}}), caps({{S_Y, 4 * b.h.xt_size + xrows}}),
+                   "B x digits");
+        check_plan(b.h.tdig, caps({{S_T1, b.h.t_size}, {S_Y, b.h.tp_size}}), caps({{S_Y, 4 * b.h.tp_size + trows}}),
+                   "B T digits");
+      }
     }
     upload(c, b.h.b1, b.b1);
     upload(c, b.h.b2, b.b2);
     if (mixed()) {
       upload(c, b.h.xsplit, b.xs);
       upload(c, b.h.tsplit, b.ts);
-      ensure(c, r->Xs, (size_t)std::max<int64_t>(b.h.xt_size, 1) * 2 * r->nsplit);
-      ensure(c, r->T2, (size_t)std::max<int64_t>(b.h.tp_size, 1) * 2 * r->nsplit);
+      upload(c, b.h.xdig, b.xd);
+      upload(c, b.h.tdig, b.td);
+      ensure(c, r->Xs, (size_t)std::max<int64_t>(b.h.xt_size, 1) * split_bytes());
+      ensure(c, r->T2, (size_t)std::max<int64_t>(b.h.tp_size, 1) * split_bytes());
     }
     ensure(c, r->T1, (size_t)b.h.t_size * 8);
     ensure(c, r->T2, (size_t)b.h.t_size * 8);
@@ -693,6 +769,23 @@ struct Eng {
   }
 
   void gemm(DevGemmBuf& g, const Bases& b, bool use_mixed, int kind = 4) {
+    if (use_mixed && r->exact) {
+      if (!r->use_tc || !prep_tc(g, b))
+        throw Err{TT_ERR_INVALID_ARG, "exact split: a GEMM plan is not eligible for the tcgen05 digit kernel"};
+      for (const GSeg& sg : g.host.segs)
+        if (sg.K > tcz_max_k())
+          throw Err{TT_ERR_INVALID_ARG, "exact split: a sector longer than " + std::to_string(tcz_max_k())};
+      if (!r->tcerr.p) {
+        ensure(c, r->tcerr, 16);
+        CK(cudaMemsetAsync(r->tcerr.p, 0, 16, st));
+      }
+      const long e = prof_begin(kind, g.d.flops);
+      CK(launch_gemm_tcz(g.d.groups, g.d.segs, (const GTile*)g.tilesp.p, g.ntilesp, g.maps.p, b, (int*)r->tcerr.p,
+                         c->wait_ns, st));
+      prof_end(e);
+      count();
+      return;
+    }
     if (use_mixed) {
       const bool tc = r->use_tc && prep_tc(g, b);
       if (g.choice < 0 || (!tc && g.choice != TK_MMA64)) {
@@ -708,6 +801,12 @@ struct Eng {
     } else {
       CK(launch_gemm_f64(g.d, b, st));
     }
+    prof_end(e);
+    count();
+  }
+  void gather_digits(const DevGatherBuf& g, const Bases& b) {
+    const long e = prof_begin(3, 0);
+    CK(launch_gather_digits(g.d, b, st));
     prof_end(e);
     count();
   }
@@ -730,32 +829,42 @@ struct Eng {
     sz[k] = n;
     (&sz == &r->Lsize ? r->Lpsize : r->Rpsize)[k] = np;
     ensure(c, v[k], (size_t)n * 8);
-    if (mixed()) ensure(c, vsp[k], (size_t)std::max<int64_t>(np, 1) * 2 * r->nsplit);
+    if (mixed()) ensure(c, vsp[k], (size_t)std::max<int64_t>(np, 1) * split_bytes());
   }
   // FP64 environment -> split-bf16 copy with rows padded to 8 elements
   void split_env(std::vector<DBuf>& v, std::vector<DBuf>& vsp, std::vector<int64_t>& sz, int k) {
     if (!mixed()) return;
     if (!r->esplit_ok[k]) {
-      CopyPlan cp = build_env_split(r->bond[k], M().chan[k]);
-      check_plan(cp, caps({{S_X, make_env_layout(r->bond[k], M().chan[k]).size},
-                           {S_Y, make_env_layout(r->bond[k], M().chan[k], true).size}}), "env split");
-      upload(c, cp, r->esplit[k]);
+      const EnvLayout E = make_env_layout(r->bond[k], M().chan[k]), P = make_env_layout(r->bond[k], M().chan[k], true);
+      if (r->exact) {
+        DigitPlan dp = build_env_digits(r->bond[k], M().chan[k]);
+        int64_t rows = 0;
+        for (int64_t q : P.rows) rows += q;
+        check_plan(dp, caps({{S_X, E.size}, {S_Y, P.size}}), caps({{S_Y, 4 * P.size + rows}}), "env digits");
+        upload(c, dp, r->edig[k]);
+      } else {
+        CopyPlan cp = build_env_split(r->bond[k], M().chan[k]);
+        check_plan(cp, caps({{S_X, E.size}, {S_Y, P.size}}), "env split");
+        upload(c, cp, r->esplit[k]);
+      }
       r->esplit_ok[k] = 1;
     }
     Bases b{};
     b.p[S_X] = v[k].p;
     b.p[S_Y] = vsp[k].p;
     b.lo[S_Y] = (&sz == &r->Lsize ? r->Lpsize : r->Rpsize)[k];
-    CK(launch_split_copy(r->esplit[k].d, b, r->nsplit, st));
+    if (r->exact) CK(launch_digit_copy(r->edig[k].d, b, st));
+    else CK(launch_split_copy(r->esplit[k].d, b, r->nsplit, st));
     count();
   }
-  // x -> transposed padded split copy for S1's B operand (Xs)
+  // x -> transposed padded split (or digit) copy for S1's B operand (Xs)
   void split_x_transposed(SiteDev& s, const double* x) {
     Bases b{};
     b.p[S_X] = (void*)x;
     b.p[S_Y] = r->Xs.p;
     b.lo[S_Y] = s.h.xt_size;
-    CK(launch_split_copy(s.xs.d, b, r->nsplit, st));
+    if (r->exact) CK(launch_digit_copy(s.xd.d, b, st));
+    else CK(launch_split_copy(s.xs.d, b, r->nsplit, st));
     count();
   }
 
@@ -765,10 +874,10 @@ struct Eng {
                                   std::to_string(bytes)};
   }
   void need_site(int j, const SiteDev& s, bool left_env_in, bool right_env_in) {
-    const int el = mixed() ? 2 * r->nsplit : 8;
+    const int64_t el = mixed() ? (int64_t)split_bytes() : 8;
     if (left_env_in) { need(r->L[j], r->Lsize[j] * 8, "L"); if (mixed()) need(r->Lsp[j], r->Lpsize[j] * el, "Lsp"); }
     if (right_env_in) { need(r->R[j + 1], r->Rsize[j + 1] * 8, "R"); if (mixed()) need(r->Rsp[j + 1], r->Rpsize[j + 1] * el, "Rsp"); }
-    if (mixed() && s.h.xt_size > 0) need(r->Xs, s.h.xt_size * 2 * r->nsplit, "Xs");  // split-BF16 plans only
+    if (mixed() && s.h.xt_size > 0) need(r->Xs, s.h.xt_size * el, "Xs");  // split-BF16 plans only
     if (left_env_in && r->Lsize[j] != make_env_layout(r->bond[j], M().chan[j]).size) throw Err{TT_ERR_STATE, "stale L"};
     if (right_env_in && r->Rsize[j + 1] != make_env_layout(r->bond[j + 1], M().chan[j + 1]).size) throw Err{TT_ERR_STATE, "stale R"};
     need(r->T1, std::max(s.h.t1_size, s.h.u1_size) * 8, "T1");
@@ -794,10 +903,10 @@ struct Eng {
       b.p[S_R] = r->Rsp[j + 1].p; b.lo[S_R] = r->Rpsize[j + 1];
       b.lo[S_T2] = s.h.t2_size;
       gemm(s.s1, b, true, 0);
-      gather(s.s2, b, 1, r->nsplit);
+      if (r->exact) gather_digits(s.s2, b);
+      else gather(s.s2, b, 1, r->nsplit);
       gemm(s.s3, b, true, 0);
     } else {
-      OzScope oz(*this, r->oz_all && !force_fp64);
       b.p[S_X] = (void*)x;
       b.p[S_L] = r->L[j].p;
       b.p[S_R] = r->R[j + 1].p;
@@ -813,7 +922,7 @@ struct Eng {
   void apply_bond(int k, const double* x, double* y) {
     BondDev& bd = bond_plan(k);
     {
-      const int el = mixed() ? 2 * r->nsplit : 8;
+      const int64_t el = mixed() ? (int64_t)split_bytes() : 8;
       int64_t e = make_env_layout(r->bond[k], M().chan[k]).size;
       if (r->Lsize[k] != e || r->Rsize[k] != e) throw Err{TT_ERR_STATE, "stale bond environments"};
       need(r->L[k], e * 8, "L");
@@ -821,7 +930,7 @@ struct Eng {
       if (mixed()) { need(r->Lsp[k], r->Lpsize[k] * el, "Lsp"); need(r->Rsp[k], r->Rpsize[k] * el, "Rsp"); }
       need(r->T1, bd.h.t_size * 8, "T1");
       need(r->T2, (mixed() ? bd.h.tp_size : bd.h.t_size) * el, "T2");
-      if (mixed()) need(r->Xs, std::max<int64_t>(bd.h.xt_size, 1) * 2 * r->nsplit, "Xs");
+      if (mixed()) need(r->Xs, std::max<int64_t>(bd.h.xt_size, 1) * el, "Xs");
     }
     Bases b{};
     b.p[S_Y] = y;
@@ -831,7 +940,8 @@ struct Eng {
         Bases bx{};
         bx.p[S_X] = (void*)x;
         bx.p[S_Y] = r->Xs.p; bx.lo[S_Y] = bd.h.xt_size;
-        CK(launch_split_copy(bd.xs.d, bx, r->nsplit, st));
+        if (r->exact) CK(launch_digit_copy(bd.xd.d, bx, st));
+        else CK(launch_split_copy(bd.xs.d, bx, r->nsplit, st));
         count();
       }
       b.p[S_X] = r->Xs.p; b.lo[S_X] = bd.h.xt_size;
@@ -842,13 +952,13 @@ struct Eng {
         Bases bt{};
         bt.p[S_T1] = r->T1.p;
         bt.p[S_Y] = r->T2.p; bt.lo[S_Y] = bd.h.tp_size;
-        CK(launch_split_copy(bd.ts.d, bt, r->nsplit, st));
+        if (r->exact) CK(launch_digit_copy(bd.td.d, bt, st));
+        else CK(launch_split_copy(bd.ts.d, bt, r->nsplit, st));
         count();
       }
       b.p[S_T2] = r->T2.p; b.lo[S_T2] = bd.h.tp_size;
       gemm(bd.b2, b, true, 2);
     } else {
-      OzScope oz(*this, r->oz_all);
       b.p[S_X] = (void*)x;
       b.p[S_L] = r->L[k].p;
       b.p[S_R] = r->R[k].p;
@@ -2016,7 +2126,7 @@ struct Eng {
       ensure(c, r->Qk, (size_t)r->ldq * r->opts.krylov_dim * 8);
       ensure(c, r->W, (size_t)r->ldq * 8);
       ensure(c, r->tmp, (size_t)r->ldq * 8);
-      ensure(c, r->Xn, (size_t)r->ldq * 3 * 2);
+      ensure(c, r->Xn, (size_t)r->ldq * 4 * 2);
     }
     auto apply = [&](const double* x, double* y) {
       Bases b{};
@@ -2146,6 +2256,7 @@ void alloc_rho_arrays(tt_rho* r) {
   r->Lpsize.assign(N + 1, 0);
   r->Rpsize.assign(N + 1, 0);
   r->esplit.assign(N + 1, DevCopyBuf());
+  r->edig.assign(N + 1, DevDigitBuf());
   r->esplit_ok.assign(N + 1, 0);
   {
     const char* gk = std::getenv("TT_GEMM_KERNEL");
@@ -2180,10 +2291,13 @@ void free_rho(tt_rho* r) {
   for (auto* v : {&r->sp, &r->sp64})
     for (auto& s : *v) {
       release(c, s.s1); release(c, s.s2); release(c, s.s3); release(c, s.s3l); release(c, s.r1); release(c, s.r2);
-      release(c, s.r3); release(c, s.xs);
+      release(c, s.r3); release(c, s.xs); release(c, s.xd);
     }
   for (auto& e : r->esplit) release(c, e);
-  for (auto& s : r->bp) { release(c, s.b1); release(c, s.b2); release(c, s.xs); release(c, s.ts); }
+  for (auto& e : r->edig) release(c, e);
+  for (auto& s : r->bp) {
+    release(c, s.b1); release(c, s.b2); release(c, s.xs); release(c, s.ts); release(c, s.xd); release(c, s.td);
+  }
   for (auto* v : {&r->qrl, &r->lqr})
     for (auto& q : *v) {
       dfree(c, q.jobs); release(c, q.gather); release(c, q.scatter); release(c, q.rout);
@@ -2196,6 +2310,10 @@ void free_rho(tt_rho* r) {
   for (DBuf* b : {&r->Qk, &r->W, &r->Xs, &r->Xn, &r->T1, &r->T2, &r->Sb, &r->ws, &r->partial, &r->ks, &r->rs, &r->tmp, &r->obs, &r->el0, &r->el1, &r->tcerr, &r->qrfb})
     dfree(c, *b);
 }
+
+// the growth stage's two-site contractions have no digit path: the exact
+// split grows in FP64
+int growth_arith(int prec) { return prec == 3 ? 0 : prec; }
 
 bool valid_opts(const tt_run_opts* o) {
   return o && o->D_max >= 1 && o->krylov_dim >= 1 && o->krylov_dim <= 16 && o->precision >= 0 && o->precision <= 3 &&
@@ -2307,7 +2425,6 @@ tt_status tt_rho_create(tt_ctx* ctx, const tt_mpo* mpo, double beta0, int taylor
   r->opts = *opts;
   r->N = mpo->mpo.N;
   r->nsplit = opts->growth_precision == 1 ? 2 : (opts->growth_precision == 2 ? 3 : 0);
-  r->oz_all = opts->growth_precision == 3;
   tt_status s = guarded(ctx, r, [&] {
     alloc_rho_arrays(r);
     Eng e(r);
@@ -2340,7 +2457,7 @@ tt_status tt_rho_grow(tt_rho* rho, const tt_mpo* mpo, double dtau, double beta_m
   if (!rho || mpo != rho->mpo || !(dtau > 0)) return TT_ERR_INVALID_ARG;
   return guarded(rho->ctx, rho, [&] {
     Eng e(rho);
-    e.set_precision(rho->opts.growth_precision);
+    e.set_precision(growth_arith(rho->opts.growth_precision));
     while (rho->beta < beta_max - 1e-12 && !e.saturated()) {
       e.grow_sweep_lr(dtau / 4);
       e.grow_sweep_rl(dtau / 4);
@@ -2356,7 +2473,7 @@ tt_status tt_rho_grow_exp(tt_rho* rho, const tt_mpo* mpo, double ratio, double b
     return TT_ERR_INVALID_ARG;
   return guarded(rho->ctx, rho, [&] {
     Eng e(rho);
-    e.set_precision(rho->opts.growth_precision);
+    e.set_precision(growth_arith(rho->opts.growth_precision));
     while (rho->beta < beta_max - 1e-12 && !e.saturated()) {
       const double dtau = std::min(rho->beta * (ratio - 1.0), beta_max - rho->beta);
       e.grow_sweep_lr(dtau / 4);
@@ -2623,8 +2740,8 @@ static tt_status heff_apply_impl(tt_ctx* ctx, const tt_mpo* mpo, int site, int p
   r->mpo = mpo;
   r->opts = tt_run_opts{1, 1, precision, precision, 1e-12, 1e-10, 0};
   r->N = mpo->mpo.N;
-  r->nsplit = (precision == 1) ? 2 : (precision == 2 ? 3 : 0);
-  r->oz_all = precision == 3;
+  r->nsplit = (precision == 1) ? 2 : (precision == 2 ? 3 : (precision == 3 ? 4 : 0));
+  r->exact = precision == 3;
   tt_status s = guarded(ctx, nullptr, [&] {
     alloc_rho_arrays(r);
     r->bond.assign(r->N + 1, Bond());

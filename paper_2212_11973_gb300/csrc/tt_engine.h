@@ -87,6 +87,8 @@ struct Caps {
 void check_plan(const GemmPlan& p, const Caps& c, const char* what);
 void check_plan(const GatherPlan& p, const Caps& c, const char* what);
 void check_plan(const CopyPlan& p, const Caps& c, const char* what);
+void check_exps(const GemmPlan& p, const Caps& ex, const char* what);
+void check_plan(const DigitPlan& p, const Caps& c, const Caps& ex, const char* what);
 
 void upload(tt_ctx* c, const GemmPlan& p, DevGemmBuf& o);
 void upload(tt_ctx* c, const GatherPlan& p, DevGatherBuf& o);
@@ -95,18 +97,28 @@ void release(tt_ctx* c, DevGemmBuf& o);
 void release(tt_ctx* c, DevGatherBuf& o);
 void release(tt_ctx* c, DevCopyBuf& o);
 
+struct DevDigitBuf {
+  DevDigit d;
+  DBuf buf;
+  DigitPlan host;
+};
+void upload(tt_ctx* c, const DigitPlan& p, DevDigitBuf& o);
+void release(tt_ctx* c, DevDigitBuf& o);
+
 struct SiteDev {
   bool valid = false;
   SitePlanHost h;
   DevGemmBuf s1, s3, s3l, r1, r3;
   DevGatherBuf s2, r2;
   DevCopyBuf xs;  // split-bf16 mode: x -> transposed padded copy (S1's B operand)
+  DevDigitBuf xd; // exact mode: the same as digits
 };
 struct BondDev {
   bool valid = false;
   BondPlanHost h;
   DevGemmBuf b1, b2;
   DevCopyBuf xs, ts;  // mixed precision: padded split copies of x and T
+  DevDigitBuf xd, td; // exact mode: digit copies of x and T
 };
 struct QrDev {
   bool valid = false;
@@ -134,7 +146,7 @@ struct tt_rho {
   tt_run_opts opts{};
   int N = 0;
   int nsplit = 0;  // 0 = FP64 operand layouts
-  bool oz_all = false;  // TT_PREC_SPLIT_EXACT: FP64 plans on the exact-accumulation split kernel
+  bool exact = false;   // TT_PREC_SPLIT_EXACT: split slots hold fixed-point digits (nsplit = 4)
   bool poisoned = false;
   double beta = 0.0;
   std::vector<tt::Bond> bond;           // N + 1
@@ -144,6 +156,7 @@ struct tt_rho {
   std::vector<int64_t> Lsize, Rsize;      // FP64 environment sizes (elements)
   std::vector<int64_t> Lpsize, Rpsize;    // split-bf16 copies: rows padded to 8 (elements per level)
   std::vector<tt::DevCopyBuf> esplit;     // per bond: FP64 environment -> padded split copy
+  std::vector<tt::DevDigitBuf> edig;      // per bond: FP64 environment -> digits (exact mode)
   std::vector<char> esplit_ok;
   bool use_tc = true;                     // tcgen05 kernel for eligible split-bf16 GEMMs
   bool use_cholqr = true;                 // CholeskyQR3 gauge (else Householder only)

@@ -35,6 +35,10 @@ struct DevCopy {
   int nitems = 0;
   int maxtiles = 0;  // largest item, in 32 x 32 tiles
 };
+struct DevDigit {
+  DItem* items = nullptr;
+  int nitems = 0;
+};
 
 // Device-side Krylov bookkeeping of one Lanczos exponential.
 struct KrylovState {
@@ -83,6 +87,20 @@ size_t tc_smem_bytes(int nsplit);
 size_t tcp_smem_bytes(int nsplit);
 cudaError_t launch_gemm_tcp(const GGroup* groups, const GSeg* segs, const GTile* tiles128x64, int ntiles,
                             const void* maps, const Bases& b, int nsplit, int* err, long long wait_ns, cudaStream_t s);
+// Exact-accumulation split GEMM on tcgen05 (tt_tcgen05z.cu): digit operands
+// (4 levels + int16 row exponents, GSeg.eA / eB), persistent 128 x 64 tiles,
+// the same maps; segments of K <= tcz_max_k(); output FP64 or two-float pairs
+// (flags bit 1).
+int tcz_max_k();
+size_t tcz_smem_bytes();
+cudaError_t launch_gemm_tcz(const GGroup* groups, const GSeg* segs, const GTile* tiles128x64, int ntiles,
+                            const void* maps, const Bases& b, int* err, long long wait_ns, cudaStream_t s);
+// Digit producers (tt_digits.cu): FP64 rows -> digit rows; the W-gather of
+// the exact path (two-float S1 outputs -> digit rows of T2, rows up to
+// gather_digits_max_cols() long).
+cudaError_t launch_digit_copy(const DevDigit& d, const Bases& b, cudaStream_t s);
+cudaError_t launch_gather_digits(const DevGather& g, const Bases& b, cudaStream_t s);
+int gather_digits_max_cols();
 // err: set to 1 by a CTA whose bounded wait (budget wait_ns) ran out.
 cudaError_t launch_gemm_tc(const GGroup* groups, const GSeg* segs, const GTile* tiles128, int ntiles,
                            const void* maps, const Bases& b, int nsplit, int* err, long long wait_ns, cudaStream_t s);

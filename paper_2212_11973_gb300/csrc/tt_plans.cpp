@@ -34,8 +34,19 @@ struct TermIndex {
 };
 }  // namespace
 
+std::vector<int64_t> env_row_starts(const EnvLayout& E) {
+  std::vector<int64_t> r(E.rows.size(), 0);
+  int64_t c = 0;
+  for (size_t b = 0; b < E.rows.size(); ++b) {
+    r[b] = c;
+    c += E.rows[b];
+  }
+  return r;
+}
+
 SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& ls, const std::vector<MpoTerm>& terms,
-                             const std::vector<Q>& chl, const std::vector<Q>& chr, bool mixed) {
+                             const std::vector<Q>& chl, const std::vector<Q>& chr, bool mixed, bool exact) {
+  exact = exact && mixed;
   SitePlanHost P;
   P.lay = make_site_layout(BL, BR, ls);
   const SiteLayout& S = P.lay;
@@ -52,18 +63,32 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
   const int d = ls.d;
 
   // ---- S1 (mixed: B = transposed x block [(s, a_r)][a_l], rows padded: K-major)
-  std::vector<int64_t> t1off(S.blk.size(), -1), t1ld(S.blk.size(), 0), xtoff(S.blk.size(), 0);
-  int64_t cur = 0, xt = 0;
+  std::vector<int64_t> t1off(S.blk.size(), -1), t1ld(S.blk.size(), 0), xtoff(S.blk.size(), 0), xtrow(S.blk.size(), 0);
+  int64_t cur = 0, xt = 0, xtr = 0;
   if (mixed)
     for (size_t bi = 0; bi < S.blk.size(); ++bi) {
       const SiteBlock& b = S.blk[bi];
       const int N = b.m * b.dr, ldt = pad8i(b.dl);
       xtoff[bi] = xt;
+      xtrow[bi] = xtr;
       // x block row-major (d_l x N) -> transposed (N x ldt)
       P.xsplit.items.push_back(CItem{mkref(S_X, b.off), mkref(S_Y, xt), N, 1, 1, ldt, b.dl, N});
       xt += (int64_t)N * ldt;
+      xtr += N;
     }
   P.xt_size = pad8l(xt);
+  // digit exponents live after the four levels of a slot (offsets in 2-byte units)
+  const int64_t xte = 4 * P.xt_size;
+  if (exact)
+    for (size_t bi = 0; bi < S.blk.size(); ++bi) {
+      const SiteBlock& b = S.blk[bi];
+      const int N = b.m * b.dr;
+      // transposed: digit row j = column j of the block, K = d_l
+      P.xdig.items.push_back(DItem{mkref(S_X, b.off), mkref(S_Y, xtoff[bi]), mkref(S_Y, xte + xtrow[bi]), 1, N,
+                                   pad8i(b.dl), 1, N, b.dl});
+    }
+  const std::vector<int64_t> elrow = env_row_starts(ELo), errow = env_row_starts(ERo);
+  const int64_t ele = 4 * ELo.size, ere = 4 * ERo.size;
   for (size_t bi = 0; bi < S.blk.size(); ++bi) {
     const SiteBlock& b = S.blk[bi];
     int64_t M = EL.rows[b.l];
@@ -74,6 +99,7 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
     P.s1.add_group((int)M, (int)N, mkref(S_T1, cur), (int)N, t1flag);
     if (mixed) P.s1.add_seg(mkref(S_L, ELo.off[b.l]), ELo.ld[b.l], 0, mkref(S_X, xtoff[bi]), pad8i(b.dl), 1, b.dl);
     else P.s1.add_seg(mkref(S_L, EL.off[b.l]), b.dl, 0, mkref(S_X, b.off), (int)N, 0, b.dl);
+    if (exact) P.s1.set_exps(mkref(S_L, ele + elrow[b.l]), 1, mkref(S_X, xte + xtrow[bi]), 1);
     cur += M * N;
   }
   P.t1_size = cur;
@@ -81,8 +107,10 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
   // ---- T2 layout (per right sector r of BR)
   const int nr = BR.nsec();
   std::vector<int64_t> t2off(nr, 0), t2cols(nr, 0), t2col((size_t)nr * nwr, -1);
-  std::vector<int> t2ket((size_t)nr * nwr, -1);
+  std::vector<int> t2ket((size_t)nr * nwr, -1), t2seg((size_t)nr * nwr, -1), nseg(nr, 0);
+  std::vector<int64_t> t2e(nr, 0);
   cur = 0;
+  int64_t curE = 0;
   for (int r = 0; r < nr; ++r) {
     int64_t cols = 0;
     for (int w = 0; w < nwr; ++w) {
@@ -90,13 +118,17 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
       if (b < 0) continue;
       t2col[(size_t)r * nwr + w] = cols;
       t2ket[(size_t)r * nwr + w] = b;
+      t2seg[(size_t)r * nwr + w] = nseg[r]++;
       cols += wpad(BR.dim[b]);
     }
     t2cols[r] = cols;
     t2off[r] = cur;
     cur += S.grp_rows[r] * cols;
+    t2e[r] = curE;  // exponents: per group row, one per column segment
+    curE += S.grp_rows[r] * nseg[r];
   }
   P.t2_size = cur;
+  const int64_t t2x = 4 * P.t2_size;
 
   // ---- S2 gather
   for (size_t obi = 0; obi < S.blk.size(); ++obi) {
@@ -134,6 +166,10 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
             P.s2.contribs.push_back(c);
           }
         it.c1 = (int)P.s2.contribs.size();
+        if (exact) {
+          it.e = mkref(S_T2, t2x + t2e[r] + (ob.grp_row + so) * nseg[r] + t2seg[(size_t)r * nwr + w2]);
+          it.e_rs = (int64_t)ob.m * nseg[r];
+        }
         P.s2.items.push_back(it);
         P.s2.elems += (double)it.rows * it.cols * (1 + it.c1 - it.c0);
       }
@@ -151,6 +187,9 @@ SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& l
         int64_t rrow = ER.row_of(b, w2);
         P.s3.add_seg(mkref(S_T2, t2off[r] + col), (int)t2cols[r], 0, mkref(S_R, ERo.off[b] + rrow * ERo.ld[b]),
                      ERo.ld[b], 1, BR.dim[b]);
+        if (exact)
+          P.s3.set_exps(mkref(S_T2, t2x + t2e[r] + t2seg[(size_t)r * nwr + w2]), nseg[r],
+                        mkref(S_R, ere + errow[b] + rrow), 1);
       }
     }
     for (int w2 = 0; w2 < nwr; ++w2) {
@@ -284,7 +323,19 @@ CopyPlan build_env_split(const Bond& B, const std::vector<Q>& chan) {
   return cp;
 }
 
-BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed) {
+DigitPlan build_env_digits(const Bond& B, const std::vector<Q>& chan) {
+  EnvLayout E = make_env_layout(B, chan), P = make_env_layout(B, chan, true);
+  const std::vector<int64_t> rs = env_row_starts(P);
+  DigitPlan dp;
+  for (int b = 0; b < B.nsec(); ++b)
+    if (E.rows[b] > 0)
+      dp.items.push_back(DItem{mkref(S_X, E.off[b]), mkref(S_Y, P.off[b]), mkref(S_Y, 4 * P.size + rs[b]), E.ld[b], 1,
+                               P.ld[b], 1, (int)E.rows[b], B.dim[b]});
+  return dp;
+}
+
+BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed, bool exact) {
+  exact = exact && mixed;
   // y_q = sum_w L_w(q <- b) x_b R_w(q <- b)^T with b = q - ch[w]: first
   // T_b = L_b x_b for all channels at once (rows (w, a) of the environment),
   // then per output sector the sum over w of (rows of channel w of T_b) R^T.
@@ -293,14 +344,17 @@ BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed
   EnvLayout Eo = make_env_layout(B, ch, mixed);  // operand layout of L and R
   P.mat = make_bondmat_layout(B);
   const int nw = (int)ch.size();
-  std::vector<int64_t> toff(B.nsec(), -1), tpoff(B.nsec(), -1), xtoff(B.nsec(), 0);
-  int64_t cur = 0, curp = 0, xt = 0;
+  std::vector<int64_t> toff(B.nsec(), -1), tpoff(B.nsec(), -1), xtoff(B.nsec(), 0), tprow(B.nsec(), 0);
+  std::vector<int64_t> xtrow(B.nsec(), 0);
+  int64_t cur = 0, curp = 0, xt = 0, xtr = 0, tpr = 0;
   for (int b = 0; b < B.nsec(); ++b) {
     const int d = B.dim[b], ldp = pad8i(d);
     if (mixed) {
       xtoff[b] = xt;
+      xtrow[b] = xtr;
       P.xsplit.items.push_back(CItem{mkref(S_X, P.mat.off[b]), mkref(S_Y, xt), d, 1, 1, ldp, d, d});
       xt += (int64_t)d * ldp;
+      xtr += d;
     }
     if (E.rows[b] == 0) continue;
     toff[b] = cur;
@@ -308,8 +362,10 @@ BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed
     if (mixed) {
       P.b1.add_seg(mkref(S_L, Eo.off[b]), Eo.ld[b], 0, mkref(S_X, xtoff[b]), ldp, 1, d);
       tpoff[b] = curp;
+      tprow[b] = tpr;
       P.tsplit.items.push_back(CItem{mkref(S_T1, cur), mkref(S_Y, curp), d, 1, ldp, 1, (int)E.rows[b], d});
       curp += E.rows[b] * ldp;
+      tpr += E.rows[b];
     } else {
       P.b1.add_seg(mkref(S_L, Eo.off[b]), Eo.ld[b], 0, mkref(S_X, P.mat.off[b]), d, 0, d);
     }
@@ -318,16 +374,40 @@ BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed
   P.t_size = cur;
   P.xt_size = pad8l(xt);
   P.tp_size = pad8l(curp);
+  const std::vector<int64_t> erow = env_row_starts(Eo);
+  const int64_t xte = 4 * P.xt_size, tpe = 4 * P.tp_size, ee = 4 * Eo.size;
+  if (exact) {
+    for (int b = 0; b < B.nsec(); ++b) {
+      const int d = B.dim[b], ldp = pad8i(d);
+      // transposed S block: digit row c = column c of S, K = d
+      P.xdig.items.push_back(DItem{mkref(S_X, P.mat.off[b]), mkref(S_Y, xtoff[b]), mkref(S_Y, xte + xtrow[b]), 1, d,
+                                   ldp, 1, d, d});
+      if (toff[b] >= 0)
+        P.tdig.items.push_back(DItem{mkref(S_T1, toff[b]), mkref(S_Y, tpoff[b]), mkref(S_Y, tpe + tprow[b]), d, 1, ldp,
+                                     1, (int)E.rows[b], d});
+    }
+    // B1 segments in group order: one per sector with rows
+    int gi = 0;
+    for (int b = 0; b < B.nsec(); ++b) {
+      if (E.rows[b] == 0) continue;
+      GSeg& sg = P.b1.segs[P.b1.groups[gi++].seg0];
+      sg.eA = mkref(S_L, ee + erow[b]);
+      sg.eas = 1;
+      sg.eB = mkref(S_X, xte + xtrow[b]);
+      sg.ebs = 1;
+    }
+  }
   for (int q = 0; q < B.nsec(); ++q) {
     P.b2.add_group(B.dim[q], B.dim[q], mkref(S_Y, P.mat.off[q]), B.dim[q], 0);
     for (int w = 0; w < nw; ++w) {
       int b = B.find(B.q[q] - ch[w]);
       if (b < 0 || toff[b] < 0) continue;
       int64_t row = E.row_of(b, w);
-      if (mixed)
+      if (mixed) {
         P.b2.add_seg(mkref(S_T2, tpoff[b] + row * pad8i(B.dim[b])), pad8i(B.dim[b]), 0,
                      mkref(S_R, Eo.off[b] + row * Eo.ld[b]), Eo.ld[b], 1, B.dim[b]);
-      else
+        if (exact) P.b2.set_exps(mkref(S_T2, tpe + tprow[b] + row), 1, mkref(S_R, ee + erow[b] + row), 1);
+      } else
         P.b2.add_seg(mkref(S_T2, toff[b] + row * B.dim[b]), B.dim[b], 0, mkref(S_R, Eo.off[b] + row * Eo.ld[b]),
                      Eo.ld[b], 1, B.dim[b]);
     }

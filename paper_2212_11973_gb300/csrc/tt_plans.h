@@ -14,9 +14,17 @@ struct SitePlanHost {
   // with rows padded to 8 elements (K-major B operand); xsplit copies x there.
   CopyPlan xsplit;
   int64_t xt_size = 0;
+  // exact mode: the same transposed x as fixed-point digits with a row
+  // exponent (int16 after the four levels of the slot)
+  DigitPlan xdig;
 };
 // FP64 environment (natural layout) -> split-bf16 copy with rows padded to 8.
 CopyPlan build_env_split(const Bond& B, const std::vector<Q>& chan);
+// FP64 environment -> digit rows (padded like the split copy), int16 row
+// exponents after the four levels, in the layout's row order.
+DigitPlan build_env_digits(const Bond& B, const std::vector<Q>& chan);
+// first row of every ket sector's matrix in the environment layout
+std::vector<int64_t> env_row_starts(const EnvLayout& E);
 
 struct BondPlanHost {
   BondMatLayout mat;
@@ -26,6 +34,7 @@ struct BondPlanHost {
   // to 8), B2's A operand the split of T with rows padded to 8
   CopyPlan xsplit, tsplit;
   int64_t xt_size = 0, tp_size = 0;
+  DigitPlan xdig, tdig;  // exact mode: digit copies of x (transposed) and of T
 };
 
 struct QrPlanHost {
@@ -48,9 +57,12 @@ struct CholQrPlan {
 };
 CholQrPlan build_cholqr(const std::vector<QrJob>& jobs, int64_t ws0);
 
+// exact (with mixed): the split-BF16 layouts carry fixed-point digits; the
+// GEMM segments get the operands' row exponents, the gather items the output
+// exponents, S1 writes two-float pairs.
 SitePlanHost build_site_plan(const Bond& BL, const Bond& BR, const LocalSpace& ls, const std::vector<MpoTerm>& terms,
-                             const std::vector<Q>& chl, const std::vector<Q>& chr, bool mixed);
-BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed);
+                             const std::vector<Q>& chl, const std::vector<Q>& chr, bool mixed, bool exact = false);
+BondPlanHost build_bond_plan(const Bond& B, const std::vector<Q>& ch, bool mixed, bool exact = false);
 GemmPlan build_absorb_left(const SiteLayout& oldl, const SiteLayout& newl, const Bond& Bold, const Bond& Bnew,
                            const std::vector<int64_t>& soff, const std::vector<int>& new_of_old);
 GemmPlan build_absorb_right(const SiteLayout& oldl, const SiteLayout& newl, const Bond& Bold, const Bond& Bnew,

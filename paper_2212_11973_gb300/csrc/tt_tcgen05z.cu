@@ -1,0 +1,333 @@
+// Exact-accumulation split GEMM on the 5th-generation tensor cores (sm_103a).
+//
+// Operands are fixed-point BF16 digits (Ozaki scheme with one exponent per
+// operand row and GEMM segment; see tt_ozaki.cu for the arithmetic): a row
+// with largest biased exponent e holds v ~ 2^(e - 1054) F, F = a0 2^24 +
+// a1 2^16 + a2 2^8 + a3, |a_s| <= 256, the four digit levels stored like
+// split-BF16 levels (K-major, rows padded to 8, level l at l * lo[slot]) and
+// the int16 exponents per row next to them.  Every tensor-core product of
+// two digits is exact and, for a segment of K <= 256, every sum of the digit
+// pairs with s + t = d is an integer below 2^24, exact in the FP32 TMEM
+// accumulator.  The kernel keeps the ten pairs with s + t <= 3 in four TMEM
+// accumulators D_0..D_3 and, once per segment, the epilogue warps add
+// sum_d D_d 2^(eA + eB - 2060 - 8 d) to a two-float (hi, lo) sum in
+// registers (TwoSum for d = 0, 1): ~2^-32 of the rows' bounds, with no
+// rounding that grows with K.
+//
+// Structure as gemm_tcp_kernel (tt_tcgen05p.cu): persistent, one CTA per SM,
+// 128 x 64 output tiles; warp 0 streams the digit tiles (A 4 x 16 KB, B 4 x
+// 8 KB per 64-wide K chunk) into two shared-memory stages, warp 1 issues the
+// MMAs of a segment into one of two TMEM buffers (4 accumulators x 64
+// columns each), warps 2-5 fold a finished buffer while the next segment's
+// MMAs run in the other, and write each finished tile as FP64 or as a two-
+// float pair (flags bit 1).  Waits are bounded as in the other tcgen05
+// kernels.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tt_kernels.h"
+#include "tt_tc_ptx.h"
+
+namespace tt {
+
+namespace {
+
+using namespace tcx;
+
+constexpr int ZBM = 128, ZBN = 64, ZBK = 64, ZDIG = 4, ZPAIRS = 10;
+constexpr int ZA_BYTES = ZBM * ZBK * 2;  // 16 KB per digit level
+constexpr int ZB_BYTES = ZBN * ZBK * 2;  // 8 KB per digit level
+constexpr int ZSTAGE_BYTES = ZDIG * (ZA_BYTES + ZB_BYTES);
+constexpr int ZSTAGES = 2;
+constexpr uint32_t ZTMEM_COLS = 512;
+constexpr int ZTHREADS = 192;
+constexpr int ZMAXK = 256;  // longest segment whose digit sums stay exact
+
+__device__ __forceinline__ void mbar_arrive_z(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool wait_z(uint64_t* bar, uint32_t parity, long long budget, volatile int* abort_f,
+                                       int* err) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_f) return false;
+    if (budget <= 0 || (long long)(globaltimer() - t0) > budget) {
+      *abort_f = 1;
+      if (err) atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float pow2z(int x) {
+  return (x >= -126 && x <= 127) ? __int_as_float((x + 127) << 23) : 0.f;
+}
+
+__device__ __forceinline__ void two_sum_z(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float ap = s - bp;
+  lo += (hi - ap) + (x - bp);
+  hi = s;
+}
+
+// digit pair p -> (s, t): d = s + t ascending, the first pair of each d at
+// p = 0, 1, 3, 6
+__device__ __forceinline__ void pair_of(int p, int& s, int& t) {
+  const int ps[ZPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+  const int pt[ZPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
+  s = ps[p];
+  t = pt[p];
+}
+
+__global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __restrict__ groups,
+                                                               const GSeg* __restrict__ segs,
+                                                               const GTile* __restrict__ tiles, int ntiles,
+                                                               const CUtensorMap* __restrict__ maps, Bases bs,
+                                                               int* __restrict__ err, long long wait_ns) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[ZSTAGES], empty_bar[ZSTAGES], accf[2], acce[2];
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s, issued_s, consumed_s, last_commit_s, last_accf_s;
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  volatile int* abort_f = &abort_s;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(ZTMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < ZSTAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 4);
+    }
+    abort_s = 0;
+    issued_s = 0;
+    consumed_s = 0;
+    last_commit_s = -1;
+    last_accf_s = -1;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int it = 0, fenced = -1;
+      for (int t = blockIdx.x; t < ntiles && !*abort_f; t += gridDim.x) {
+        const GTile tl = tiles[t];
+        const GGroup g = groups[tl.g];
+        for (int si = g.seg0; si < g.seg1 && !*abort_f; ++si) {
+          const int K = segs[si].K;
+          const CUtensorMap* ma = maps + 3 * si;
+          const CUtensorMap* mb = maps + 3 * si + 2;
+          if (fenced != si) {
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(ma))
+                         : "memory");
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mb))
+                         : "memory");
+            fenced = si;
+          }
+          for (int k0 = 0; k0 < K; k0 += ZBK) {
+            const int s = it % ZSTAGES;
+            if (!wait_z(&empty_bar[s], ((it / ZSTAGES) & 1) ^ 1, wait_ns, abort_f, err)) break;
+            uint8_t* st = smem + s * ZSTAGE_BYTES;
+            mbar_expect_tx(&full_bar[s], ZSTAGE_BYTES);
+#pragma unroll
+            for (int l = 0; l < ZDIG; ++l) tma_load_3d(st + l * ZA_BYTES, ma, k0, tl.m0, l, &full_bar[s]);
+#pragma unroll
+            for (int l = 0; l < ZDIG; ++l)
+              tma_load_3d(st + ZDIG * ZA_BYTES + l * ZB_BYTES, mb, k0, tl.n0, l, &full_bar[s]);
+            ++it;
+            issued_s = it;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: one fold unit per segment ----------------
+    if (lane == 0) {
+      const uint32_t idesc =
+          (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ZBN >> 3) << 17) | ((uint32_t)(ZBM >> 4) << 24);
+      int it = 0, fg = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const GTile tl = tiles[t];
+        const GGroup g = groups[tl.g];
+        for (int si = g.seg0; si < g.seg1 && ok; ++si) {
+          const int nch = (segs[si].K + ZBK - 1) / ZBK;
+          const int b = fg & 1;
+          ok = wait_z(&acce[b], ((fg >> 1) & 1) ^ 1, wait_ns, abort_f, err);
+          if (!ok) break;
+          fence_after();
+          const uint32_t tb = tmem + 256 * b;
+          for (int c = 0; c < nch; ++c) {
+            const int s = it % ZSTAGES;
+            ok = wait_z(&full_bar[s], (it / ZSTAGES) & 1, wait_ns, abort_f, err);
+            if (!ok) break;
+            consumed_s = it + 1;
+            fence_after();
+            const uint32_t sa = smem_u32(smem + s * ZSTAGE_BYTES);
+#pragma unroll
+            for (int p = 0; p < ZPAIRS; ++p) {
+              int ls, lt;
+              pair_of(p, ls, lt);
+              const bool first = (p == 0 || p == 1 || p == 3 || p == 6);
+              const uint32_t aa = sa + ls * ZA_BYTES, ba = sa + ZDIG * ZA_BYTES + lt * ZB_BYTES;
+              const uint32_t dst = tb + 64 * (ls + lt);
+#pragma unroll
+              for (int kk = 0; kk < ZBK / 16; ++kk) {
+                const uint32_t acc = (c > 0 || kk > 0 || !first) ? 1u : 0u;
+                umma_f16(dst, make_desc(aa + kk * 32), make_desc(ba + kk * 32), idesc, acc);
+              }
+            }
+            umma_commit(&empty_bar[s]);
+            last_commit_s = it;
+            ++it;
+          }
+          if (!ok) break;
+          umma_commit(&accf[b]);
+          last_accf_s = fg;
+          ++fg;
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: fold per segment, write per tile ----------------
+    const int q = warp & 3;
+    const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    int fg = 0;
+    bool ok = true;
+    float hi[ZBN], lo[ZBN], dv[ZDIG][16];
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const GTile tl = tiles[t];
+      const GGroup g = groups[tl.g];
+      const int row = tl.m0 + 32 * q + lane;
+#pragma unroll
+      for (int i = 0; i < ZBN; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+      for (int si = g.seg0; si < g.seg1; ++si) {
+        const GSeg sg = segs[si];
+        const int b = fg & 1;
+        ok = __all_sync(0xffffffffu, wait_z(&accf[b], (fg >> 1) & 1, wait_ns, abort_f, err));
+        if (!ok) break;
+        fence_after();
+        const int ea = row < g.M
+                           ? (int)reinterpret_cast<const short*>(bs.p[slot_of(sg.eA)])[off_of(sg.eA) + (long long)row * sg.eas]
+                           : 0;
+        const short* eBp = reinterpret_cast<const short*>(bs.p[slot_of(sg.eB)]) + off_of(sg.eB);
+        const uint32_t tb = tmem + 256 * b;
+#pragma unroll
+        for (int cb = 0; cb < ZBN; cb += 16) {
+#pragma unroll
+          for (int d = 0; d < ZDIG; ++d) tmem_ld16(tb + 64 * d + lane_off + cb, dv[d]);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int col = tl.n0 + cb + i;
+            const int eb = col < g.N ? (int)eBp[(long long)col * sg.ebs] : 0;
+            const int x = ea + eb - 2060;
+            two_sum_z(hi[cb + i], lo[cb + i], dv[0][i] * pow2z(x));
+            two_sum_z(hi[cb + i], lo[cb + i], dv[1][i] * pow2z(x - 8));
+            lo[cb + i] += dv[2][i] * pow2z(x - 16) + dv[3][i] * pow2z(x - 24);
+          }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_z(&acce[b]);
+        ++fg;
+      }
+      if (!ok) break;
+      if (row < g.M) {
+        const bool accum = g.flags & 1, out_pair = g.flags & 2;
+        const long long o = (long long)row * g.ldc + tl.n0;
+        const int ncol = min(ZBN, g.N - tl.n0);
+        if (out_pair) {
+          float2* Cp = reinterpret_cast<float2*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+#pragma unroll
+          for (int i = 0; i < ZBN; ++i)
+            if (i < ncol) Cp[i] = make_float2(hi[i], lo[i]);
+        } else {
+          double* Cp = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+#pragma unroll
+          for (int i = 0; i < ZBN; ++i)
+            if (i < ncol) {
+              const double v = (double)hi[i] + (double)lo[i];
+              Cp[i] = accum ? Cp[i] + v : v;
+            }
+        }
+      }
+    }
+  }
+
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (abort_s && tid == 0) {
+    for (int c = consumed_s; c < issued_s; ++c) mbar_wait(&full_bar[c % ZSTAGES], (c / ZSTAGES) & 1, DRAIN_NS);
+    if (last_commit_s >= 0) mbar_wait(&empty_bar[last_commit_s % ZSTAGES], (last_commit_s / ZSTAGES) & 1, DRAIN_NS);
+    if (last_accf_s >= 0) mbar_wait(&accf[last_accf_s & 1], (last_accf_s >> 1) & 1, DRAIN_NS);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ZTMEM_COLS) : "memory");
+}
+
+int sm_count_z() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return 148;
+    }
+    return v;
+  }();
+  return n;
+}
+
+}  // namespace
+
+int tcz_max_k() { return ZMAXK; }
+size_t tcz_smem_bytes() { return (size_t)ZSTAGES * ZSTAGE_BYTES + 1024; }
+
+cudaError_t launch_gemm_tcz(const GGroup* groups, const GSeg* segs, const GTile* tiles, int ntiles, const void* maps,
+                            const Bases& b, int* err, long long wait_ns, cudaStream_t s) {
+  if (ntiles == 0) return cudaSuccess;
+  const size_t smem = tcz_smem_bytes();
+  static const cudaError_t e =
+      cudaFuncSetAttribute(gemm_tcz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int grid = ntiles < sm_count_z() ? ntiles : sm_count_z();
+  gemm_tcz_kernel<<<grid, ZTHREADS, smem, s>>>(groups, segs, tiles, ntiles, (const CUtensorMap*)maps, b, err, wait_ns);
+  return cudaGetLastError();
+}
+
+}  // namespace tt
