@@ -556,7 +556,10 @@ def main():
                                for k in ("site_exp", "bond_exp", "env_update", "absorb", "gauge")},
         "profiled_s_per_step": s["step_ms"] / 1e3 / nprof if s.get("step_ms") else None,
         "qr_gauge": {"sectors_per_step": s["qr_sectors"] / nprof,
-                     "householder_fallbacks_per_step": s["qr_fallbacks"] / nprof},
+                     "householder_fallbacks_per_step": s["qr_fallbacks"] / nprof,
+                     "gemm_ms_per_step": s["qr_gemm_ms"] / nprof,
+                     "gemm_fp64_tflops": (s["qr_gemm_flops"] / (s["qr_gemm_ms"] / 1e3) / 1e12) if s["qr_gemm_ms"] else None,
+                     "cholesky_ms_per_step": s["qr_chol_ms"] / nprof},
         "mixed_vs_fp64": check,
         "autotune": {"plans_tcgen05_128x128": s["tuned_tc128"], "plans_tcgen05_persistent_128x64": s["tuned_tcp128x64"],
                      "plans_mma_sync_64x64": s["tuned_mma64"]},

@@ -158,6 +158,9 @@ typedef struct {
      tcgen05 128 x 128 tiles, persistent tcgen05 128 x 64 tiles, mma.sync
      64 x 64 tiles */
   long long tuned_tc128, tuned_tcp128x64, tuned_mma64;
+  /* inside qr_ms (profiling mode): the CholeskyQR3 Gram / apply GEMMs (time
+     and algorithmic flops) and the Cholesky + triangular-inverse kernels */
+  double qr_gemm_ms, qr_gemm_flops, qr_chol_ms;
 } tt_stats;
 
 /* ---- context ---------------------------------------------------------- */

@@ -5,8 +5,10 @@
 // v_k ~ 2^(e - 1054) (a0 2^24 + a1 2^16 + a2 2^8 + a3), e the largest biased
 // FP64 exponent of the row, and e itself as an int16 next to the levels.
 //  * digit_copy_kernel: FP64 rows (any row / element stride) -> digit rows
-//    padded for TMA; one warp per row when elements are contiguous, one warp
-//    per 32 rows (lanes along the rows, coalesced reads) otherwise.
+//    padded for TMA; one CTA per group of 32 rows of an item; a warp per row
+//    when elements are contiguous, else lanes along the rows (coalesced
+//    reads) and warps along K with the row exponent combined in shared
+//    memory.
 //  * gather_digits_kernel: the W-gather of the exact path: sums of two-float
 //    (hi, lo) S1 outputs times MPO coefficients in two-float arithmetic
 //    (TwoProd by FMA, TwoSum), then digits of every output row segment.
@@ -72,36 +74,49 @@ __device__ __forceinline__ long long fixed_of_pair(float hi, float lo, int emax)
 
 constexpr int DT = 256;
 
+// One CTA per (item, group of 32 digit rows): grid (items, max row groups).
 __global__ void __launch_bounds__(DT) digit_copy_kernel(const DItem* __restrict__ items, Bases bs) {
   const DItem it = items[blockIdx.x];
+  const int r0 = blockIdx.y * 32;
+  if (r0 >= it.rows) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double* src = reinterpret_cast<const double*>(bs.p[slot_of(it.src)]) + off_of(it.src);
   __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(bs.p[slot_of(it.dst)]) + off_of(it.dst);
   short* ex = reinterpret_cast<short*>(bs.p[slot_of(it.e)]) + off_of(it.e);
   const long long lo = bs.lo[slot_of(it.dst)];
   if (it.s_k == 1) {
-    // contiguous rows: a warp per row, lanes along K
-    for (int r = warp; r < it.rows; r += DT / 32) {
-      const double* s = src + (long long)r * it.s_r;
+    // contiguous rows: each warp takes 4 of the 32 rows, lanes along K
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + warp * 4 + q;
+      if (r >= it.rows) break;
+      const double* sp = src + (long long)r * it.s_r;
       int m = 0;
-      for (int k = lane; k < it.cols; k += 32) m = max(m, dexp(s[k]));
+      for (int k = lane; k < it.cols; k += 32) m = max(m, dexp(sp[k]));
       m = __reduce_max_sync(0xffffffffu, m);
-      for (int k = lane; k < it.cols; k += 32) put_digits(fixed_of_double(s[k], m), dst + (long long)r * it.dst_rs + k, lo);
+      for (int k = lane; k < it.cols; k += 32)
+        put_digits(fixed_of_double(sp[k], m), dst + (long long)r * it.dst_rs + k, lo);
       if (lane == 0) ex[(long long)r * it.e_rs] = (short)m;
     }
   } else {
-    // strided rows (e.g. a transposed block): lanes along the rows
-    for (int r0 = warp * 32; r0 < it.rows; r0 += DT) {
-      const int r = r0 + lane;
-      const bool in = r < it.rows;
-      int m = 0;
-      for (int k = 0; k < it.cols; ++k)
-        if (in) m = max(m, dexp(src[(long long)r * it.s_r + (long long)k * it.s_k]));
-      for (int k = 0; k < it.cols; ++k)
-        if (in)
-          put_digits(fixed_of_double(src[(long long)r * it.s_r + (long long)k * it.s_k], m),
-                     dst + (long long)r * it.dst_rs + k, lo);
-      if (in) ex[(long long)r * it.e_rs] = (short)m;
+    // strided rows (a transposed block): lanes along the 32 rows (coalesced
+    // reads along the source row), warps split K, the row exponent combined
+    // in shared memory
+    __shared__ int emax_s[32];
+    if (threadIdx.x < 32) emax_s[threadIdx.x] = 0;
+    __syncthreads();
+    const int r = r0 + lane;
+    const bool in = r < it.rows;
+    const double* sp = src + (long long)r * it.s_r;
+    int m = 0;
+    if (in)
+      for (int k = warp; k < it.cols; k += DT / 32) m = max(m, dexp(sp[(long long)k * it.s_k]));
+    if (in) atomicMax(&emax_s[lane], m);
+    __syncthreads();
+    const int e = emax_s[lane];
+    if (in) {
+      for (int k = warp; k < it.cols; k += DT / 32)
+        put_digits(fixed_of_double(sp[(long long)k * it.s_k], e), dst + (long long)r * it.dst_rs + k, lo);
+      if (warp == 0) ex[(long long)r * it.e_rs] = (short)e;
     }
   }
 }
@@ -164,7 +179,7 @@ __global__ void __launch_bounds__(DT) gather_digits_kernel(const GItem* __restri
 
 cudaError_t launch_digit_copy(const DevDigit& d, const Bases& b, cudaStream_t s) {
   if (d.nitems == 0) return cudaSuccess;
-  digit_copy_kernel<<<d.nitems, DT, 0, s>>>(d.items, b);
+  digit_copy_kernel<<<dim3(d.nitems, d.maxgroups > 0 ? d.maxgroups : 1), DT, 0, s>>>(d.items, b);
   return cudaGetLastError();
 }
 

@@ -167,6 +167,8 @@ void upload(tt_ctx* c, const DigitPlan& p, DevDigitBuf& o) {
   CK(cudaStreamSynchronize(c->st));
   o.d.items = (DItem*)o.buf.p;
   o.d.nitems = (int)p.items.size();
+  o.d.maxgroups = 0;
+  for (const DItem& it : p.items) o.d.maxgroups = std::max(o.d.maxgroups, (it.rows + 31) / 32);
   o.host = p;
 }
 void release(tt_ctx* c, DevDigitBuf& o) { dfree(c, o.buf); o.d = DevDigit(); o.host = DigitPlan(); }
@@ -1086,13 +1088,21 @@ struct Eng {
     }
     CK(cudaMemsetAsync(q.fail.p, 0, q.h.jobs.size() * sizeof(int), st));
     for (int p = 0; p < 3; ++p) {
+      long e = prof_begin(11, q.gram[p].d.flops);
       CK(launch_gemm_f64(q.gram[p].d, b, st));
+      prof_end(e);
+      e = prof_begin(12, 0);
       CK(launch_chol_inv((const CholJob*)q.cjobs[p].p, q.ncj[p], dptr(r->ws), (int*)q.fail.p, st));
+      prof_end(e);
+      e = prof_begin(11, q.app[p].d.flops);
       CK(launch_gemm_f64(q.app[p].d, b, st));
+      prof_end(e);
       count(3);
     }
+    const long e2 = prof_begin(11, q.tt.d.flops + q.rf.d.flops);
     CK(launch_gemm_f64(q.tt.d, b, st));
     CK(launch_gemm_f64(q.rf.d, b, st));
+    prof_end(e2);
     count(2);
     if (!r->qrfb.p) {
       ensure(c, r->qrfb, 16);
@@ -2500,7 +2510,7 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
       rho->launches_acc = 0;
       rho->qr_sectors_acc = 0;
       rho->evused = 0;
-      for (int k = 0; k < 11; ++k) { rho->kind_ms[k] = 0; rho->kind_n[k] = 0; rho->kind_flops[k] = 0; }
+      for (int k = 0; k < 13; ++k) { rho->kind_ms[k] = 0; rho->kind_n[k] = 0; rho->kind_flops[k] = 0; }
       CK(cudaEventRecord(rho->ev0, st));
     }
     if (rho->graph && (rho->graph_dtau != dtau || rho->graph_prof != rho->prof ||
@@ -2519,7 +2529,7 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
       // profiling events of the captured step live in their own pool, created
       // before the capture
       rho->gused = 0;
-      for (int k = 0; k < 11; ++k) rho->graph_kind_flops[k] = 0;
+      for (int k = 0; k < 13; ++k) rho->graph_kind_flops[k] = 0;
       if (rho->prof)
         while (rho->gpool.size() < rho->evused + 512) {
           cudaEvent_t x;
@@ -2638,7 +2648,7 @@ tt_status tt_stats_get(const tt_rho* rho_c, tt_stats* out) {
         rho->kind_ms[rho->gkind[i]] += t * rho->graph_replays;
         rho->kind_n[rho->gkind[i]] += rho->graph_replays;
       }
-      for (int k = 0; k < 11; ++k) rho->kind_flops[k] += rho->graph_kind_flops[k] * rho->graph_replays;
+      for (int k = 0; k < 13; ++k) rho->kind_flops[k] += rho->graph_kind_flops[k] * rho->graph_replays;
     }
     rho->graph_replays = 0;
     rho->stats.heff_ms = rho->kind_ms[0];
@@ -2655,6 +2665,9 @@ tt_status tt_stats_get(const tt_rho* rho_c, tt_stats* out) {
     rho->stats.env_update_ms = rho->kind_ms[8];
     rho->stats.absorb_ms = rho->kind_ms[9];
     rho->stats.gauge_ms = rho->kind_ms[10];
+    rho->stats.qr_gemm_ms = rho->kind_ms[11];
+    rho->stats.qr_gemm_flops = rho->kind_flops[11];
+    rho->stats.qr_chol_ms = rho->kind_ms[12];
     rho->stats.qr_fallbacks = 0;
     if (rho->qrfb.p) {
       int nfb = 0;

@@ -174,7 +174,8 @@ struct tt_rho {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool stats_pending = false;
   // per-launch CUDA events (profiling mode): kind 0 = site H_eff GEMMs,
-  // 1 = environment GEMMs, 2 = bond H_eff GEMMs, 3 = gather, 4 = other
+  // 1 = environment GEMMs, 2 = bond H_eff GEMMs, 3 = gather, 4 = other,
+  // 5 = QR gauge, 6..10 = sweep phases, 11 = QR GEMMs, 12 = Cholesky kernels
   bool prof = false;
   // CUDA graph of one beta-step (the block structure is fixed in 1-TDVP)
   cudaGraphExec_t graph = nullptr;
@@ -189,13 +190,13 @@ struct tt_rho {
   std::vector<cudaEvent_t> gpool;         // profiling events recorded inside the graph
   std::vector<int> gkind;
   size_t gused = 0;
-  double graph_kind_flops[11] = {0};
+  double graph_kind_flops[13] = {0};
   std::vector<cudaEvent_t> evpool;
   std::vector<int> evkind;
   size_t evused = 0;
-  double kind_ms[11] = {0};
-  long long kind_n[11] = {0};
-  double kind_flops[11] = {0};
+  double kind_ms[13] = {0};
+  long long kind_n[13] = {0};
+  double kind_flops[13] = {0};
   double heff_flops_acc = 0, step_flops_acc = 0;
   long long launches_acc = 0;
   long long qr_sectors_acc = 0, graph_qr_sectors = 0;

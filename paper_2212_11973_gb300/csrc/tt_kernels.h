@@ -38,6 +38,7 @@ struct DevCopy {
 struct DevDigit {
   DItem* items = nullptr;
   int nitems = 0;
+  int maxgroups = 0;  // largest item, in groups of 32 digit rows
 };
 
 // Device-side Krylov bookkeeping of one Lanczos exponential.

@@ -65,7 +65,8 @@ class tt_stats(C.Structure):
                 ("qr_ms", C.c_double), ("bond_flops", C.c_double), ("qr_sectors", C.c_longlong), ("qr_fallbacks", C.c_longlong),
                 ("site_exp_ms", C.c_double), ("bond_exp_ms", C.c_double), ("env_update_ms", C.c_double),
                 ("absorb_ms", C.c_double), ("gauge_ms", C.c_double),
-                ("tuned_tc128", C.c_longlong), ("tuned_tcp128x64", C.c_longlong), ("tuned_mma64", C.c_longlong)]
+                ("tuned_tc128", C.c_longlong), ("tuned_tcp128x64", C.c_longlong), ("tuned_mma64", C.c_longlong),
+                ("qr_gemm_ms", C.c_double), ("qr_gemm_flops", C.c_double), ("qr_chol_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -49,8 +49,11 @@ CLUSTER_2x2_FULL = replace(CLUSTER_2x2, name="2x2 open cluster U=4 mu=0 untrunca
 CYL_4x8_D256 = Workload("CL4x8 U=8 1/8 doping D=256 FP64", 8, 4, True, 1.0, 8.0, MU_EIGHTH_DOPING, 1, 256, 0.01,
                         0.05, 10.0, 8, 0)
 CYL_4x8_D512 = replace(CYL_4x8_D256, name="CL4x8 U=8 1/8 doping D=512 mixed", D=512, precision=2)
-CYL_6x12_D1024 = Workload("CL6x12 U=8 1/8 doping D=1024 mixed", 12, 6, True, 1.0, 8.0, MU_EIGHTH_DOPING, 1, 1024,
-                          0.01, 0.05, 12.0, 8, 2)
+# The headline workload runs the exact-accumulation split (precision 3): the
+# split-BF16 x6 mode misses the 1e-6 accuracy bar at this size (see bench.py
+# --precision 2).
+CYL_6x12_D1024 = Workload("CL6x12 U=8 1/8 doping D=1024 mixed (exact-split BF16 digits)", 12, 6, True, 1.0, 8.0,
+                          MU_EIGHTH_DOPING, 1, 1024, 0.01, 0.05, 12.0, 8, 3)
 LADDER_2x4 = Workload("2x4 ladder U=4 mu=-0.3 D=32", 4, 2, False, 1.0, 4.0, -0.3, 1, 32, 0.01, 0.05, 1.0)
 
 BATCH_SEED = 2212119730

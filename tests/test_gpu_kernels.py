@@ -58,14 +58,17 @@ def test_heff_split_bf16_matches_fp64(tt, D):
     keeps ~2^-16 of every operand, x6 ~2^-24 with FP32 tensor-core
     accumulation (worst case ~gamma_K relative to sum |a_k b_k|, which for
     random-sign data stays a few times 2^-24 of the group's largest entry);
-    the exact split keeps 32 bits of every row / column bound per 32-wide K
-    tile and sums exactly, ~2^-32 times a small factor."""
+    the exact split keeps 32 bits of every row bound per GEMM segment and sums
+    exactly: per product ~2^-32 max_row|a| max_col|b|, over K random-sign
+    terms ~2^-32 sqrt(K) max|a| max|b| against ~sqrt(K) rms|a| rms|b| for the
+    result, so (max / rms)^2 ~ 16 for Gaussian data times a few for the
+    two-float intermediates: ~4e-9 relative."""
     ctx = tt.Context()
     mpo = tt.Mpo(ctx, 8, 2, False, t=1.0, U=4.0, mu=-0.3, form=1)
     SL, SR, L, R, x = _inputs(tt, mpo, 7, D, 11 * D)
     y0 = tt.heff_apply_host(ctx, mpo, 7, 0, SL, SR, L, R, x)
     assert np.isfinite(y0).all() and np.abs(y0).max() > 0
-    for prec, tol_norm, tol_el in ((1, 3e-5, 3e-4), (2, 1e-6, 1e-5), (3, 1e-9, 1e-8)):
+    for prec, tol_norm, tol_el in ((1, 3e-5, 3e-4), (2, 1e-6, 1e-5), (3, 5e-9, 1e-8)):
         y = tt.heff_apply_host(ctx, mpo, 7, prec, SL, SR, L, R, x)
         err = np.linalg.norm(y - y0) / np.linalg.norm(y0)
         el = _groupwise_err(y, y0, SL, SR)
@@ -119,6 +122,6 @@ def test_heff_full_size_mixed_vs_fp64(tt):
     err3 = np.linalg.norm(y3 - y0) / np.linalg.norm(y0)
     el3 = _groupwise_err(y3, y0, SL, SR)
     print("full-size exact-split relative error", err3, "group-wise", el3)
-    assert err3 < 1e-9 and el3 < 1e-8, (err3, el3)
+    assert err3 < 5e-9 and el3 < 1e-8, (err3, el3)  # bound as in test_heff_split_bf16_matches_fp64
     mpo.close()
     ctx.close()
