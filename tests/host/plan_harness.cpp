@@ -9,7 +9,9 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <stdexcept>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -111,9 +113,82 @@ std::vector<double> pad_env(const Bond& B, const std::vector<Q>& ch, const doubl
   return out;
 }
 
+// Exact-split exponent bookkeeping: producers (digit copies, digit gather)
+// record, per exponent slot element, which data row it describes (slot, first
+// element, length); consumers (GEMM segments) must read, for every operand
+// row, the exponent recorded for exactly that row, covering their K.
+struct ExpBook {
+  std::map<std::pair<int, int64_t>, std::tuple<int, int64_t, int>> rows;
+  static int slot(Ref r) { return (int)(r >> 56); }
+  static int64_t off(Ref r) { return (int64_t)(r & 0x00FFFFFFFFFFFFFFull); }
+  void produce(Ref e, int64_t e_rs, Ref dst, int64_t dst_rs, int nrows, int cols, int as_slot) {
+    for (int r = 0; r < nrows; ++r) {
+      auto key = std::make_pair(as_slot, off(e) + r * e_rs);
+      auto val = std::make_tuple(as_slot, off(dst) + r * dst_rs, cols);
+      auto it = rows.find(key);
+      if (it != rows.end() && it->second != val)
+        throw std::runtime_error("two producers write exponent " + std::to_string(key.second) + " of slot " +
+                                 std::to_string(as_slot));
+      rows[key] = val;
+    }
+  }
+  void consume(Ref e, int es, Ref data, int ld, int nrows, int K, const char* what) {
+    if (es <= 0) throw std::runtime_error(std::string("missing exponents: ") + what);
+    for (int m = 0; m < nrows; ++m) {
+      auto it = rows.find(std::make_pair(slot(e), off(e) + (int64_t)m * es));
+      if (it == rows.end())
+        throw std::runtime_error(std::string(what) + ": no exponent produced for row " + std::to_string(m));
+      const auto want = std::make_tuple(slot(data), off(data) + (int64_t)m * ld, 0);
+      if (std::get<0>(it->second) != std::get<0>(want) || std::get<1>(it->second) != std::get<1>(want))
+        throw std::runtime_error(std::string(what) + ": row " + std::to_string(m) + " reads the exponent of another row");
+      if (std::get<2>(it->second) < K)
+        throw std::runtime_error(std::string(what) + ": segment K exceeds the row the exponent covers");
+    }
+  }
+  void produce_digits(const DigitPlan& p, int as_slot) {
+    for (const DItem& it : p.items) produce(it.e, it.e_rs, it.dst, it.dst_rs, it.rows, it.cols, as_slot);
+  }
+  void consume_gemm(const GemmPlan& p, const char* what) {
+    for (const GGroup& g : p.groups)
+      for (int si = g.seg0; si < g.seg1; ++si) {
+        const GSeg& sg = p.segs[si];
+        if (sg.tA != 0 || sg.tB != 1) throw std::runtime_error(std::string(what) + ": digit operands must be K-major");
+        consume(sg.eA, sg.eas, sg.A, sg.lda, g.M, sg.K, what);
+        consume(sg.eB, sg.ebs, sg.B, sg.ldb, g.N, sg.K, what);
+      }
+  }
+};
+
 }  // namespace
 
 extern "C" {
+
+// Exact-split plans of site j (H_eff apply) and bond j+1 (bond apply): every
+// GEMM operand row reads the exponent its producer wrote for that row.
+int h_exact_exponents(const int* geom, const double* par, int j, const int* nsec_lr, const int* qn, const int* qs,
+                      const int* qd) {
+  return guarded([&] {
+    Mpo M = model(geom, par);
+    Bond BL = bond_from(qn, qs, qd, nsec_lr[0]);
+    Bond BR = bond_from(qn + nsec_lr[0], qs + nsec_lr[0], qd + nsec_lr[0], nsec_lr[1]);
+    SitePlanHost P = build_site_plan(BL, BR, M.ls, M.site[j].terms, M.chan[j], M.chan[j + 1], true, true);
+    ExpBook site;
+    site.produce_digits(P.xdig, S_X);                                 // x (transposed) -> S1's B operand
+    site.produce_digits(build_env_digits(BL, M.chan[j]), S_L);        // L -> S1's A operand
+    site.produce_digits(build_env_digits(BR, M.chan[j + 1]), S_R);    // R -> S3's B operand
+    for (const GItem& it : P.s2.items) site.produce(it.e, it.e_rs, it.dst, it.dst_rs, it.rows, it.cols, S_T2);
+    site.consume_gemm(P.s1, "S1");
+    site.consume_gemm(P.s3, "S3");
+    BondPlanHost B = build_bond_plan(BR, M.chan[j + 1], true, true);
+    ExpBook bond;
+    bond.produce_digits(B.xdig, S_X);
+    bond.produce_digits(B.tdig, S_T2);
+    bond.produce_digits(build_env_digits(BR, M.chan[j + 1]), S_L);
+    bond.produce_digits(build_env_digits(BR, M.chan[j + 1]), S_R);
+    bond.consume_gemm(B.b1, "B1");
+    bond.consume_gemm(B.b2, "B2");
+  });
+}
 
 const char* h_error() { return g_err.c_str(); }
 

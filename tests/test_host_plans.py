@@ -360,3 +360,17 @@ def test_absorb_plans_match_dense_products(h, side):
     Xd, Sd = site_to_dense(x, SL, SR), bondmat_to_dense(S, B)
     ref = np.tensordot(Sd, Xd, axes=([1], [0])) if side == 0 else np.tensordot(Xd, Sd, axes=([3], [0]))
     assert np.abs(site_to_dense(y, SL, SR) - ref).max() < 1e-12 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("geo,j,D", CASES + [((4, 2, False, 1), 3, 300)])
+def test_exact_split_exponents_follow_their_rows(h, geo, j, D):
+    """Exact-accumulation split plans: every digit operand row of every GEMM
+    segment (S1, S3, B1, B2) reads the int16 exponent that its producer (digit
+    copy of x, of T, of the environments, or the digit W-gather) wrote for
+    exactly that row, and that row covers the segment's K."""
+    Lx, Wy, per, form = geo
+    m = Model(h, Lx, Wy, per, 1.0, 4.0, -0.3, form, TP.get(geo, 0.0))
+    SL, SR = _random_bonds(D, 17 + j)
+    qn, qs, qd = _secs_arrays(SL, SR)
+    h.h_exact_exponents.argtypes = [_PI, _PD, C.c_int, _PI, _PI, _PI, _PI]
+    _chk(h, h.h_exact_exponents(m.geom, m.par, j, _ia([len(SL), len(SR)]), qn, qs, qd))
