@@ -62,11 +62,16 @@ __device__ __forceinline__ long long fixed_of_double(double v, int emax) {
   return (bits >> 63) ? -F : F;
 }
 
+// 2^x for -126 <= x <= 127 from the exponent field
+__device__ __forceinline__ float p2f(int x) { return __int_as_float((x + 127) << 23); }
+
 // F = round((hi + lo) 2^(1054 - emax)) for a two-float value, |hi + lo| < 2^(emax - 1022)
 __device__ __forceinline__ long long fixed_of_pair(float hi, float lo, int emax) {
   if (emax == 0) return 0;
-  const int sh = 1054 - emax;  // scale exponent, |hi| 2^sh < 2^32
-  const float S = ldexpf(hi, sh), Sl = ldexpf(lo, sh);
+  const int sh = 1054 - emax;  // scale exponent, |hi| 2^sh < 2^32; two exact power-of-2 factors in range
+  const int sa = sh / 2, sb = sh - sa;
+  const float fa = p2f(sa), fb = p2f(sb);
+  const float S = (hi * fa) * fb, Sl = (lo * fa) * fb;
   const float R = rintf(S);
   const float f = (S - R) + Sl;
   return (long long)R + (long long)rintf(f);

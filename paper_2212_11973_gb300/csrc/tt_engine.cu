@@ -525,6 +525,8 @@ struct Eng {
           if (J.g + (int64_t)J.parts * J.n * J.n > wsz || J.parts < 1 || J.r + (int64_t)J.n * J.n > wsz || J.ri + (int64_t)J.n * J.n > wsz)
             throw Err{TT_ERR_STATE, "Cholesky job outside the workspace"};
         q.ncj[p] = (int)cp.cj[p].size();
+        q.maxn[p] = 0;
+        for (const CholJob& cj : cp.cj[p]) q.maxn[p] = std::max(q.maxn[p], cj.n);
         ensure(c, q.cjobs[p], cp.cj[p].size() * sizeof(CholJob) + 16);
         if (!cp.cj[p].empty())
           CK(cudaMemcpyAsync(q.cjobs[p].p, cp.cj[p].data(), cp.cj[p].size() * sizeof(CholJob), cudaMemcpyHostToDevice,
@@ -1092,7 +1094,7 @@ struct Eng {
       CK(launch_gemm_f64(q.gram[p].d, b, st));
       prof_end(e);
       e = prof_begin(12, 0);
-      CK(launch_chol_inv((const CholJob*)q.cjobs[p].p, q.ncj[p], dptr(r->ws), (int*)q.fail.p, st));
+      CK(launch_chol_inv((const CholJob*)q.cjobs[p].p, q.ncj[p], dptr(r->ws), (int*)q.fail.p, st, q.maxn[p]));
       prof_end(e);
       e = prof_begin(11, q.app[p].d.flops);
       CK(launch_gemm_f64(q.app[p].d, b, st));

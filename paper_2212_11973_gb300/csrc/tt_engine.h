@@ -129,6 +129,7 @@ struct QrDev {
   DevGemmBuf gram[3], app[3], tt, rf;
   DBuf cjobs[3], fail;
   int ncj[3] = {0, 0, 0};
+  int maxn[3] = {0, 0, 0};  // largest sector (columns) of each pass's Cholesky jobs
 };
 struct MeasDev {
   bool valid = false;

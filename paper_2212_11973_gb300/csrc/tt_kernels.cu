@@ -734,6 +734,137 @@ __device__ __forceinline__ void qr_one(const QrJob J, double* __restrict__ ws) {
   }
 }
 
+// The same Cholesky + inverse with the matrix in shared memory: the upper
+// triangle packed row by row (row i holds columns i..n-1), factorised in
+// place (right-looking, a warp per trailing row, lanes along the columns),
+// R written out, then inverted in place column by column (LAPACK trti2 order:
+// column j of R^-1 = -R^-1(0:j, 0:j) R(0:j, j) / R(j, j), the product with the
+// already inverted leading block as a parallel triangular mat-vec).  Used when
+// every sector of the launch has n <= CHOL_SMEM_MAXN.
+constexpr int CHOL_SMEM_MAXN = 230;
+
+__device__ __forceinline__ int pk(int i, int j, int n) { return i * n - (i * (i - 1)) / 2 + (j - i); }
+
+__global__ void __launch_bounds__(256) chol_inv_smem_kernel(const CholJob* __restrict__ jobs, double* __restrict__ ws,
+                                                            int* __restrict__ fail) {
+  extern __shared__ double sm[];
+  const CholJob J = jobs[blockIdx.x];
+  const int n = J.n;
+  if (J.shift == 3) {
+    if (threadIdx.x == 0) fail[J.sec] = 1;
+    return;
+  }
+  if (fail[J.sec]) return;
+  double* G = ws + J.g;
+  double* R = ws + J.r;
+  double* Ri = ws + J.ri;
+  double* tmp = sm + (n * (n + 1)) / 2;  // n doubles
+  const long long nn = (long long)n * n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  __shared__ double piv, red[8];
+  __shared__ int bad;
+  // G = sum of the partial Gram matrices, upper triangle into shared memory
+  for (int i = warp; i < n; i += nw)
+    for (int j = i + lane; j < n; j += 32) {
+      const long long e = (long long)i * n + j;
+      double acc = G[e];
+      for (int s = 1; s < J.parts; ++s) acc += G[s * nn + e];
+      sm[pk(i, j, n)] = acc;
+    }
+  __syncthreads();
+  if (J.shift == 2) {
+    // last pass: G = I + E; first-order factor when n max|E| <= 1e-8, else a
+    // full factorisation; far from I (> 1e-3): Householder fallback
+    double mx = 0.0;
+    for (int i = warp; i < n; i += nw)
+      for (int j = i + lane; j < n; j += 32) {
+        const double dev = fabs(sm[pk(i, j, n)] - (i == j ? 1.0 : 0.0));
+        mx = (dev <= mx) ? mx : (dev == dev ? dev : 1e300);
+      }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[warp] = mx;
+    __syncthreads();
+    double all = 0.0;
+    for (int q = 0; q < nw; ++q) all = fmax(all, red[q]);
+    if (!(all <= 1e-3)) {
+      if (tid == 0) fail[J.sec] = 1;
+      return;
+    }
+    if ((double)n * all <= 1e-8) {
+      for (long long e = tid; e < nn; e += blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        if (j < i) {
+          R[e] = 0.0;
+          Ri[e] = 0.0;
+        } else if (j == i) {
+          const double h = 0.5 * (sm[pk(i, i, n)] - 1.0);
+          R[e] = 1.0 + h;
+          Ri[e] = 1.0 - h;
+        } else {
+          const double g = sm[pk(i, j, n)];
+          R[e] = g;
+          Ri[e] = -g;
+        }
+      }
+      return;
+    }
+  }
+  if (tid == 0) {
+    bad = 0;
+    if (J.shift == 1) {
+      // shift s = 11 (m n + n (n + 1)) u ||X||^2 with ||X||^2 <= tr(G)
+      double tr = 0.0;
+      for (int i = 0; i < n; ++i) tr += sm[pk(i, i, n)];
+      const double sft = 11.0 * ((double)J.m * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * tr;
+      for (int i = 0; i < n; ++i) sm[pk(i, i, n)] += sft;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      const double d = sm[pk(k, k, n)];
+      if (!(d > 0.0) || !isfinite(d)) {
+        bad = 1;
+        fail[J.sec] = 1;
+      }
+      piv = bad ? 1.0 : sqrt(d);
+    }
+    __syncthreads();
+    if (bad) return;
+    const double p = piv;
+    for (int j = k + tid; j < n; j += blockDim.x) sm[pk(k, j, n)] /= p;
+    __syncthreads();
+    for (int i = k + 1 + warp; i < n; i += nw) {
+      const double rki = sm[pk(k, i, n)];
+      for (int j = i + lane; j < n; j += 32) sm[pk(i, j, n)] -= rki * sm[pk(k, j, n)];
+    }
+    __syncthreads();
+  }
+  for (long long e = tid; e < nn; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    R[e] = (j >= i) ? sm[pk(i, j, n)] : 0.0;
+  }
+  __syncthreads();
+  // in-place inverse of the upper triangle, column by column
+  for (int j = 0; j < n; ++j) {
+    const double ajj = 1.0 / sm[pk(j, j, n)];
+    // tmp(0:j) = Rinv(0:j, 0:j) R(0:j, j), rows in parallel
+    for (int i = tid; i < j; i += blockDim.x) {
+      double acc = 0.0;
+      for (int q = i; q < j; ++q) acc = fma(sm[pk(i, q, n)], sm[pk(q, j, n)], acc);
+      tmp[i] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < j; i += blockDim.x) sm[pk(i, j, n)] = -ajj * tmp[i];
+    if (tid == 0) sm[pk(j, j, n)] = ajj;
+    __syncthreads();
+  }
+  for (long long e = tid; e < nn; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    Ri[e] = (j >= i) ? sm[pk(i, j, n)] : 0.0;
+  }
+}
+
 __global__ void dot_finalize(const double* partial, int nblk, double* out) {
   __shared__ double s;
   finalize_sums(partial, nblk, 1, &s);
@@ -1064,8 +1195,18 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(const CholJob* __restrict
   }
 }
 
-cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s) {
+cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s, int maxn) {
   if (njobs == 0) return cudaSuccess;
+  if (maxn > 0 && maxn <= CHOL_SMEM_MAXN) {
+    const size_t smem = ((size_t)maxn * (maxn + 1) / 2 + maxn) * sizeof(double);
+    // once per process (thread-safe static initialisation): the largest size
+    static const cudaError_t e = cudaFuncSetAttribute(
+        chol_inv_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)(((size_t)CHOL_SMEM_MAXN * (CHOL_SMEM_MAXN + 1) / 2 + CHOL_SMEM_MAXN) * sizeof(double)));
+    if (e != cudaSuccess) return e;
+    chol_inv_smem_kernel<<<njobs, 256, smem, s>>>(jobs, ws, fail);
+    return cudaGetLastError();
+  }
   chol_inv_kernel<<<njobs, 256, 0, s>>>(jobs, ws, fail);
   return cudaGetLastError();
 }

@@ -135,7 +135,8 @@ cudaError_t launch_qr_job(const QrJob& job, double* ws, cudaStream_t s);
 cudaError_t launch_qr_masked(const QrJob* jobs, int njobs, double* ws, const int* only, int* nrun, cudaStream_t s);
 // Cholesky + triangular inverse per job (shifted on request); fail[sec] set on
 // a non-positive pivot.
-cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s);
+// maxn: the largest n of the jobs (shared-memory variant up to 230).
+cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s, int maxn = 0);
 // Sign fix diag(R) >= 0 done inside launch_qr.
 
 // Per-block item of the local measurement (d = 4 local space, <= 4 pairs).

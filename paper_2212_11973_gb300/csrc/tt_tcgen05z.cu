@@ -20,7 +20,8 @@
 // MMAs of a segment into one of two TMEM buffers (4 accumulators x 64
 // columns each), warps 2-5 fold a finished buffer while the next segment's
 // MMAs run in the other, and write each finished tile as FP64 or as a two-
-// float pair (flags bit 1).  Waits are bounded as in the other tcgen05
+// float pair (flags bit 1) through a shared-memory staging buffer (coalesced
+// row stores).  Waits are bounded as in the other tcgen05
 // kernels.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -45,6 +46,9 @@ constexpr int ZSTAGES = 2;
 constexpr uint32_t ZTMEM_COLS = 512;
 constexpr int ZTHREADS = 192;
 constexpr int ZMAXK = 256;  // longest segment whose digit sums stay exact
+// epilogue staging: 128 rows x 32 columns of 8-byte outputs (33-word rows
+// against bank conflicts), after the two TMA stages
+constexpr int ZSTG_BYTES = ZBM * 33 * 8;
 
 __device__ __forceinline__ void mbar_arrive_z(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __r
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[ZSTAGES], empty_bar[ZSTAGES], accf[2], acce[2];
   __shared__ uint32_t tmem_base_s;
-  __shared__ int abort_s, issued_s, consumed_s, last_commit_s, last_accf_s;
+  __shared__ int abort_s, issued_s, consumed_s, last_commit_s, last_accf_s, epi_fail_s;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   volatile int* abort_f = &abort_s;
 
@@ -131,6 +135,7 @@ __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __r
     consumed_s = 0;
     last_commit_s = -1;
     last_accf_s = -1;
+    epi_fail_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
@@ -263,24 +268,51 @@ __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __r
         if (lane == 0) mbar_arrive_z(&acce[b]);
         ++fg;
       }
-      if (!ok) break;
-      if (row < g.M) {
+      // the four epilogue warps agree before the staging barriers: a warp that
+      // gave up (abort) still arrives here, and then all of them leave
+      if (lane == 0 && !ok) atomicExch(&epi_fail_s, 1);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (*reinterpret_cast<volatile int*>(&epi_fail_s)) {
+        ok = false;
+        break;
+      }
+      // the finished tile through shared memory, 32 columns at a time, so that
+      // a warp stores 32 consecutive columns of one row per instruction
+      {
         const bool accum = g.flags & 1, out_pair = g.flags & 2;
-        const long long o = (long long)row * g.ldc + tl.n0;
+        uint64_t* stg = reinterpret_cast<uint64_t*>(smem + ZSTAGES * ZSTAGE_BYTES);
+        const int r_loc = 32 * q + lane;
         const int ncol = min(ZBN, g.N - tl.n0);
-        if (out_pair) {
-          float2* Cp = reinterpret_cast<float2*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
 #pragma unroll
-          for (int i = 0; i < ZBN; ++i)
-            if (i < ncol) Cp[i] = make_float2(hi[i], lo[i]);
-        } else {
-          double* Cp = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+        for (int h2 = 0; h2 < ZBN; h2 += 32) {
 #pragma unroll
-          for (int i = 0; i < ZBN; ++i)
-            if (i < ncol) {
-              const double v = (double)hi[i] + (double)lo[i];
-              Cp[i] = accum ? Cp[i] + v : v;
+          for (int i = 0; i < 32; ++i) {
+            uint64_t bits;
+            if (out_pair) {
+              const float2 v = make_float2(hi[h2 + i], lo[h2 + i]);
+              bits = *reinterpret_cast<const uint64_t*>(&v);
+            } else {
+              bits = (uint64_t)__double_as_longlong((double)hi[h2 + i] + (double)lo[h2 + i]);
             }
+            stg[r_loc * 33 + i] = bits;
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+          const int col = h2 + lane;
+          for (int rr = warp - 2; rr < ZBM; rr += 4) {
+            const int grow = tl.m0 + rr;
+            if (grow < g.M && col < ncol) {
+              const long long o = (long long)grow * g.ldc + tl.n0 + col;
+              const uint64_t bits = stg[rr * 33 + lane];
+              if (out_pair) {
+                reinterpret_cast<uint64_t*>(reinterpret_cast<float2*>(bs.p[slot_of(g.C)]) + off_of(g.C))[o] = bits;
+              } else {
+                double* Cp = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+                const double v = __longlong_as_double((long long)bits);
+                *Cp = accum ? *Cp + v : v;
+              }
+            }
+          }
+          asm volatile("bar.sync 1, 128;" ::: "memory");
         }
       }
     }
@@ -316,7 +348,7 @@ int sm_count_z() {
 }  // namespace
 
 int tcz_max_k() { return ZMAXK; }
-size_t tcz_smem_bytes() { return (size_t)ZSTAGES * ZSTAGE_BYTES + 1024; }
+size_t tcz_smem_bytes() { return (size_t)ZSTAGES * ZSTAGE_BYTES + ZSTG_BYTES + 1024; }
 
 cudaError_t launch_gemm_tcz(const GGroup* groups, const GSeg* segs, const GTile* tiles, int ntiles, const void* maps,
                             const Bases& b, int* err, long long wait_ns, cudaStream_t s) {
