@@ -203,6 +203,19 @@ def cpu_baseline(D_all: int = 512, D_one: int = 256, window: bool = True) -> dic
     return out
 
 
+def batch_oracle_sample(w):
+    """A real oracle 1-TDVP beta-step of one batch ladder from its compact
+    initial state: seconds."""
+    from oracle import model as om
+    from oracle import mpo as ompo
+    from oracle import tantrg as ot
+    m = om.Model(w.Lx, w.Wy, w.periodic, w.t, w.U, w.mu, w.form)
+    st = ot.init_state(ompo.hubbard_mpo(m), w.beta0)
+    t0 = time.perf_counter()
+    ot.tdvp1_step(st, w.dtau, K=w.krylov)
+    return time.perf_counter() - t0
+
+
 def reference_arm(args):
     """The oracle timed on the host cores; each 'step' is one bounded sample
     (a dense D = 512 site apply scaled to the D = 1024 beta-step)."""
@@ -294,7 +307,9 @@ def run_batch(args):
                 b.step(w0.dtau, 1)
             ev1.record(stream)
             torch.cuda.synchronize()
-        launches = sum(b.stats(i)["launches"] for i in range(b.n))
+        st_all = [b.stats(i) for i in range(b.n)]
+        launches = sum(x["launches"] for x in st_all)
+        flops = sum(x["step_flops"] for x in st_all)
         t_dev = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
         per_step = t_dev / args.steps
         torch.cuda.synchronize()
@@ -307,6 +322,24 @@ def run_batch(args):
         b.close()
         ctx.close()
     if rank == 0:
+        peaks = _peaks()
+        peak = peaks["bf16_tflops_sustained"] if peaks else 1700.0
+        achieved = flops / (t_dev) / 1e12 if t_dev > 0 else None
+        roofline = {"bound": "tensor", "kernel": "all contractions of the batch step (64 concurrent instances, "
+                                                  "split-BF16 GEMMs with FP64-class environment updates)",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak if achieved else None,
+                    "flops_per_step": flops / args.steps, "traffic": None,
+                    "peak_note": "of measured (bf16 sustained)" if peaks else "of fallback",
+                    "note": "algorithmic flops of every instance's contractions over the device time of the timed "
+                            "batch steps; the instances' graphs run concurrently"}
+        cpu = None
+        if not args.no_cpu_baseline:
+            tw = batch_oracle_sample(ws[0])
+            cpu = {"value": tw * len(ws), "unit": "s/beta-step (batch of 64)", "cores": os.cpu_count(),
+                   "blas_threads": _blas_threads(), "kind": "oracle", "estimate": True,
+                   "sample": f"one real oracle 1-TDVP beta-step of ladder instance 0 (U={ws[0].U:.3f}, "
+                             f"mu={ws[0].mu:.3f}) from its compact rho_h(beta0), times {len(ws)} instances"}
         line = {"metric": "s per beta-step of the 64-ladder batch", "value": per_step / world,
                 "unit": "s/beta-step (batch of 64)", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": per_step * 1e3 / world, "higher_is_better": False, "scaling": "weak",
@@ -319,7 +352,7 @@ def run_batch(args):
                 "instances_per_s": 64 * world / per_step,
                 "e2e": {"value": e2e / world, "unit": "s/beta-step (batch of 64)", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 64 * 64, "includes": "tt_batch_step + tt_batch_measure"},
-                "gpu_launches": launches, "clocks": clk.summary(), "roofline": None, "cpu_baseline": None,
+                "gpu_launches": launches, "clocks": clk.summary(), "roofline": roofline, "cpu_baseline": cpu,
                 "observables_instance0": {k: obs[0][k] for k in ("beta", "energy_per_site", "density",
                                                                   "double_occ")}}
         print(json.dumps(line), flush=True)
