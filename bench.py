@@ -407,6 +407,8 @@ def main():
     ap.add_argument("--workload", default="cl6x12",
                     choices=["cl6x12", "cl4x8", "cl4x8-mixed", "batch64", "heff-apply"])
     ap.add_argument("--window", type=int, default=3, help="beta-steps of the mixed-vs-FP64 window")
+    ap.add_argument("--env-precision", type=int, default=0, choices=[-1, 0, 1, 2],
+                    help="tt_run_opts.env_precision of the mixed run (0: exact split, 2: double-float)")
     ap.add_argument("--save", default=None, help="write the prepared state (checkpoint) to this path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true",
@@ -453,7 +455,8 @@ def main():
         mpo = tt.Mpo(ctx, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
         t_prep = time.perf_counter()
         gD = min(args.grow_D, D)
-        rho = tt.Rho(ctx, mpo, cfg.beta0, tt.run_opts(gD, cfg.krylov, prec, growth_precision=prec))
+        rho = tt.Rho(ctx, mpo, cfg.beta0, tt.run_opts(gD, cfg.krylov, prec, growth_precision=prec,
+                                                      env_precision=args.env_precision))
         rho.grow(cfg.dtau, 1.0)
         if gD < D:
             rho.pad(D)
@@ -516,7 +519,7 @@ def main():
         check = None
         if not args.no_fp64_check and rank == 0:
             nw = max(args.window, 3)
-            rm = tt.Rho.load(ctx, mpo, ck0, tt.run_opts(D, cfg.krylov, prec))
+            rm = tt.Rho.load(ctx, mpo, ck0, tt.run_opts(D, cfg.krylov, prec, env_precision=args.env_precision))
             rm.step(cfg.dtau, nw)
             om = rm.measure()
             rm.close()
@@ -577,6 +580,7 @@ def main():
         "vs_baseline": None, "dtype": {0: "f64", 1: "bf16x3+f64", 2: "bf16x6+f64", 3: "bf16-exact-split+f64"}[prec], "data": "synthetic",
         "config": {"workload": cfg.name, "N": cfg.N, "D": D, "max_bond": max(dims), "dtau": cfg.dtau,
                    "krylov": cfg.krylov, "U": cfg.U, "mu": cfg.mu, "parallelism": f"replicas x{world}",
+                   "env_precision": args.env_precision,
                    "prep": f"2-TDVP growth at D={gD}, padded to D={D}, {args.warmup} warm-up steps ({t_prep:.1f} s)",
                    "l2": "state larger than L2 (no flush)"},
         "heff_tflops": heff_tflops, "env_tflops": (env_fl / (env_ms / 1e3) / 1e12) if env_ms > 0 else None,
@@ -591,11 +595,14 @@ def main():
         "qr_gauge": {"sectors_per_step": s["qr_sectors"] / nprof,
                      "householder_fallbacks_per_step": s["qr_fallbacks"] / nprof,
                      "gemm_ms_per_step": s["qr_gemm_ms"] / nprof,
-                     "gemm_fp64_tflops": (s["qr_gemm_flops"] / (s["qr_gemm_ms"] / 1e3) / 1e12) if s["qr_gemm_ms"] else None,
+                     "gemm_tflops": (s["qr_gemm_flops"] / (s["qr_gemm_ms"] / 1e3) / 1e12) if s["qr_gemm_ms"] else None,
+                     "gemm_arithmetic": "fp64" if prec == 0 else "double-float (FP32 pipe)",
                      "cholesky_ms_per_step": s["qr_chol_ms"] / nprof},
         "mixed_vs_fp64": check,
-        "autotune": {"plans_tcgen05_128x128": s["tuned_tc128"], "plans_tcgen05_persistent_128x64": s["tuned_tcp128x64"],
-                     "plans_mma_sync_64x64": s["tuned_mma64"]},
+        "autotune": ({"plans_tcgen05_128x128": s["tuned_tc128"], "plans_tcgen05_persistent_128x64": s["tuned_tcp128x64"],
+                      "plans_mma_sync_64x64": s["tuned_mma64"]} if prec in (1, 2) else
+                     {"note": "the exact split runs every digit GEMM on the persistent digit kernel; the autotuner "
+                              "chooses among the split-BF16 kernels (precisions 1 and 2)"}),
         "gpu_launches": s_plain["launches"], "roofline": roofline, "cpu_baseline": cpu,
         "clocks": clk.summary(), "clocks_profiled_pass": clk_prof.summary(),
         "observables": {k: obs[k] for k in ("beta", "energy_per_site", "density", "double_occ",

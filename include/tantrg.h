@@ -109,7 +109,9 @@ typedef struct {
   int env_precision;    /* environment updates.  0 (default): FP64 in the FP64
                            mode, the exact-accumulation split (as
                            TT_PREC_SPLIT_EXACT) in the other modes; 1: native
-                           FP64 GEMMs; -1: the arithmetic of `precision`.
+                           FP64 GEMMs; 2: double-float GEMMs on the FP32 pipe
+                           (~2^-46 per operation) in the mixed modes; -1: the
+                           arithmetic of `precision`.
                            Each update feeds the next along the chain, so its
                            rounding errors compound over the N sites (FP32-
                            class split products leave ~1e-5 in the energy at
@@ -261,9 +263,14 @@ tt_status tt_rho_bond_sectors(const tt_rho* rho, int k, int* qn, int* qs, int* d
  * Instance i is the model models[i] at bond dimension D_max[i], initialised
  * like tt_rho_create (taylor order 1, beta0) with the other fields of opts.
  * Every instance owns a context, a CUDA stream and its captured beta-step
- * graph; tt_batch_step waits for the work already queued on ctx's stream,
- * replays all instances concurrently, and makes ctx's stream wait for all of
- * them (asynchronous, like tt_tdvp_step).  tt_batch_grow runs the growth stage
+ * graph; tt_batch_step waits for the work already queued on ctx's stream and
+ * on the instance streams, steps all instances concurrently, and makes ctx's
+ * stream and the instance streams wait for the result (asynchronous, like
+ * tt_tdvp_step).  Its first step runs per instance on the instance streams
+ * (capturing their graphs); later steps with the same dtau launch one parent
+ * graph on ctx's stream that holds every instance's step graph as a child
+ * node (re-composed when an instance's graph was re-captured; per-instance
+ * steps while profiling).  tt_batch_grow runs the growth stage
  * of every instance (synchronous).  tt_batch_measure writes n tt_obs (host,
  * caller-owned; synchronises).  On error the message names the instance; the
  * batch is then only safe to destroy.  The library owns the batch; free it with

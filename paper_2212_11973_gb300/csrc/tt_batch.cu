@@ -1,10 +1,14 @@
 // Batch of independent tanTRG instances (many small models evolved together).
 //
 // Every instance is an ordinary tt_rho with its own context and CUDA stream,
-// so its beta-step is its own captured CUDA graph; a batch step forks all
-// instance streams from the caller's stream, replays every instance's graph,
-// and joins them back.  The instances share nothing, so their graphs run
-// concurrently and together fill the GPU that one small instance cannot.
+// and its beta-step is captured as its own CUDA graph.  The batch composes
+// the instances' step graphs as child nodes of one parent graph (no edges
+// between them: the instances share nothing), so a batch beta-step is one
+// graph launch on the caller's stream and the device runs every instance's
+// kernels concurrently, filling the GPU that one small instance cannot.  The
+// first step of a batch (and any step after an instance's graph was replaced,
+// or with profiling on) runs per instance on the instance streams, forked
+// from and joined back to the caller's stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +33,11 @@ struct tt_batch {
   };
   std::vector<Inst> inst;
   cudaEvent_t fork = nullptr;
+  // parent graph of one batch beta-step, and the instances' graph generations
+  // it was composed from
+  cudaGraphExec_t parent = nullptr;
+  double parent_dtau = 0.0;
+  std::vector<unsigned long long> parent_gen;
 };
 
 namespace {
@@ -66,6 +75,98 @@ tt_status for_each_instance(tt_batch* b, F&& f) {
   for (auto& t : pool) t.join();
   for (size_t i = 0; i < n; ++i)
     if (st[i] != TT_OK) return fail_inst(b, i, st[i]);
+  return TT_OK;
+}
+
+void drop_parent(tt_batch* b) {
+  if (b->parent) cudaGraphExecDestroy(b->parent);
+  b->parent = nullptr;
+}
+
+bool parent_current(const tt_batch* b, double dtau) {
+  if (!b->parent || b->parent_dtau != dtau) return false;
+  for (size_t i = 0; i < b->inst.size(); ++i)
+    if (!tt::rho_graph_current(b->inst[i].rho, dtau) || b->inst[i].rho->graph_gen != b->parent_gen[i]) return false;
+  return true;
+}
+
+// The parent graph from every instance's current step graph; none (and the
+// per-instance path) when some instance has no replayable graph.
+void build_parent(tt_batch* b, double dtau) {
+  drop_parent(b);
+  for (const auto& in : b->inst)
+    if (!tt::rho_graph_current(in.rho, dtau)) return;
+  cudaGraph_t pg = nullptr;
+  if (cudaGraphCreate(&pg, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  bool ok = true;
+  for (const auto& in : b->inst) {
+    cudaGraphNode_t node;
+    if (cudaGraphAddChildGraphNode(&node, pg, nullptr, 0, in.rho->graph_tmpl) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+  }
+  if (ok && cudaGraphInstantiate(&b->parent, pg, 0) != cudaSuccess) {
+    b->parent = nullptr;
+    ok = false;
+  }
+  if (!ok) cudaGetLastError();
+  cudaGraphDestroy(pg);
+  if (!b->parent) return;
+  b->parent_dtau = dtau;
+  b->parent_gen.resize(b->inst.size());
+  for (size_t i = 0; i < b->inst.size(); ++i) b->parent_gen[i] = b->inst[i].rho->graph_gen;
+}
+
+// n beta-steps, one per instance on its own stream (forked from and joined
+// back to the caller's stream); captures the instances' graphs when needed
+tt_status step_per_instance(tt_batch* b, double dtau, int n) {
+  if (cudaEventRecord(b->fork, b->ctx->st) != cudaSuccess) {
+    cudaGetLastError();
+    b->ctx->err = "batch fork event failed";
+    return TT_ERR_CUDA;
+  }
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    tt_batch::Inst& in = b->inst[i];
+    if (cudaStreamWaitEvent(in.st, b->fork, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return fail_inst(b, i, TT_ERR_CUDA);
+    }
+    tt_status s = tt_tdvp_step(in.rho, in.mpo, dtau, n);
+    if (s != TT_OK) return fail_inst(b, i, s);
+    if (cudaEventRecord(in.done, in.st) != cudaSuccess || cudaStreamWaitEvent(b->ctx->st, in.done, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return fail_inst(b, i, TT_ERR_CUDA);
+    }
+  }
+  return TT_OK;
+}
+
+// n replays of the parent graph on the caller's stream, ordered after all
+// earlier work of the instance streams and before all later work on them
+tt_status step_parent(tt_batch* b, double dtau, int n) {
+  cudaStream_t st = b->ctx->st;
+  try {
+    for (size_t i = 0; i < b->inst.size(); ++i) {
+      tt_batch::Inst& in = b->inst[i];
+      if (cudaEventRecord(in.done, in.st) != cudaSuccess || cudaStreamWaitEvent(st, in.done, 0) != cudaSuccess)
+        throw tt::Err{TT_ERR_CUDA, "batch join event failed"};
+    }
+    for (auto& in : b->inst) tt::rho_account_replays(in.rho, dtau, n, st, true);
+    for (int s = 0; s < n; ++s)
+      if (cudaGraphLaunch(b->parent, st) != cudaSuccess) throw tt::Err{TT_ERR_CUDA, "batch graph launch failed"};
+    for (auto& in : b->inst) tt::rho_account_replays(in.rho, dtau, n, st, false);
+    if (cudaEventRecord(b->fork, st) != cudaSuccess) throw tt::Err{TT_ERR_CUDA, "batch fork event failed"};
+    for (auto& in : b->inst)
+      if (cudaStreamWaitEvent(in.st, b->fork, 0) != cudaSuccess) throw tt::Err{TT_ERR_CUDA, "batch fork event failed"};
+  } catch (const tt::Err& e) {
+    cudaGetLastError();
+    b->ctx->err = e.msg;
+    return e.st;
+  }
   return TT_OK;
 }
 
@@ -119,6 +220,7 @@ tt_status tt_batch_create(tt_ctx* ctx, int n, const tt_model* models, const int*
 
 void tt_batch_destroy(tt_batch* b) {
   if (!b) return;
+  drop_parent(b);
   for (auto& in : b->inst) destroy_inst(in);
   if (b->fork) cudaEventDestroy(b->fork);
   delete b;
@@ -145,25 +247,18 @@ tt_status tt_batch_pad(tt_batch* b) {
 
 tt_status tt_batch_step(tt_batch* b, double dtau, int n_steps) {
   if (!b || !(dtau > 0) || n_steps < 0) return TT_ERR_INVALID_ARG;
-  if (cudaEventRecord(b->fork, b->ctx->st) != cudaSuccess) {
-    cudaGetLastError();
-    b->ctx->err = "batch fork event failed";
-    return TT_ERR_CUDA;
+  int s = 0;
+  if (n_steps > 0 && !parent_current(b, dtau)) {
+    // one step per instance (captures or re-captures the instance graphs),
+    // then the parent graph from them when every instance has one
+    tt_status r = step_per_instance(b, dtau, 1);
+    if (r != TT_OK) return r;
+    s = 1;
+    build_parent(b, dtau);
   }
-  for (size_t i = 0; i < b->inst.size(); ++i) {
-    tt_batch::Inst& in = b->inst[i];
-    if (cudaStreamWaitEvent(in.st, b->fork, 0) != cudaSuccess) {
-      cudaGetLastError();
-      return fail_inst(b, i, TT_ERR_CUDA);
-    }
-    tt_status s = tt_tdvp_step(in.rho, in.mpo, dtau, n_steps);
-    if (s != TT_OK) return fail_inst(b, i, s);
-    if (cudaEventRecord(in.done, in.st) != cudaSuccess || cudaStreamWaitEvent(b->ctx->st, in.done, 0) != cudaSuccess) {
-      cudaGetLastError();
-      return fail_inst(b, i, TT_ERR_CUDA);
-    }
-  }
-  return TT_OK;
+  if (s == n_steps) return TT_OK;
+  if (!b->parent) return step_per_instance(b, dtau, n_steps - s);
+  return step_parent(b, dtau, n_steps - s);
 }
 
 tt_status tt_batch_measure(tt_batch* b, tt_obs* out_n) {

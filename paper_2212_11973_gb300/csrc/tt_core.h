@@ -241,6 +241,9 @@ struct QrJob {
 struct CholJob {
   int64_t g, r, ri;
   int m, n, shift, sec, parts;
+  // packed upper-triangle scratch (n (n + 1) / 2 elements) for sectors too
+  // large for shared memory
+  int64_t pk = 0;
 };
 
 }  // namespace tt

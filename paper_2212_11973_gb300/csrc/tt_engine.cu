@@ -274,15 +274,15 @@ struct Eng {
 
   const Mpo& M() const { return r->mpo->mpo; }
   bool mixed() const { return r->nsplit > 0; }
-  // FP64 GEMM plans run on the exact-accumulation split kernel (tt_ozaki.cu)
-  // instead of FP64 FMA while set (env updates in the mixed modes, every
-  // contraction of the linear stage in TT_PREC_SPLIT_EXACT)
-  bool oz_now = false;
+  // kernel of the FP64 GEMM plans while set (the environment updates of the
+  // mixed modes): 0 FP64 FMA, 1 the exact-accumulation split (tt_ozaki.cu),
+  // 2 double-float on the FP32 pipe (gemm_df_kernel)
+  int f64_kernel = 0;
   struct OzScope {
     Eng& e;
-    bool saved;
-    OzScope(Eng& eng, bool on) : e(eng), saved(eng.oz_now) { e.oz_now = on; }
-    ~OzScope() { e.oz_now = saved; }
+    int saved;
+    OzScope(Eng& eng, int k) : e(eng), saved(eng.f64_kernel) { e.f64_kernel = k; }
+    ~OzScope() { e.f64_kernel = saved; }
   };
   double* dptr(DBuf& b) { return (double*)b.p; }
 
@@ -294,6 +294,11 @@ struct Eng {
       cudaGraphExecDestroy(r->graph);
       r->graph = nullptr;
     }
+    if (r->graph_tmpl) {
+      cudaGraphDestroy(r->graph_tmpl);
+      r->graph_tmpl = nullptr;
+    }
+    ++r->graph_gen;
   }
 
   void invalidate_bond(int k) {
@@ -369,9 +374,13 @@ struct Eng {
   }
   // environment updates in split-BF16 (else FP64 plans, also in mixed mode)
   bool env_mixed() const { return mixed() && !r->exact && r->opts.env_precision == -1; }
-  // FP64 environment plans on the exact-accumulation split kernel
-  // (tt_ozaki.cu): the default in every split mode
-  bool env_oz() const { return mixed() && !env_mixed() && r->opts.env_precision != 1; }
+  // kernel of the FP64 environment plans (f64_kernel values): the exact-
+  // accumulation split by default in every split mode, double-float with
+  // env_precision 2, FP64 FMA with 1
+  int env_f64_kernel() const {
+    if (!mixed() || env_mixed()) return 0;
+    return r->opts.env_precision == 0 ? 1 : (r->opts.env_precision == 2 ? 2 : 0);
+  }
   // bytes per element of a split slot (levels, plus the int16 row exponents
   // of the digit layouts, never more rows than elements)
   size_t split_bytes() const { return (size_t)2 * (r->nsplit + (r->exact ? 1 : 0)); }
@@ -428,9 +437,14 @@ struct Eng {
       check_plan(h.xdig, caps({{S_X, n}, {S_Y, h.xt_size}}), caps({{S_Y, 4 * h.xt_size + xrows}}), "x digits");
       check_plan(h.s2, caps({{S_T1, h.t1_size}, {S_T2, h.t2_size}}), "S2");
       if (t2e > 4 * h.t2_size + h.t2_size) throw Err{TT_ERR_STATE, "T2 exponents exceed the slot"};
-      for (const GItem& it : h.s2.items)
+      for (const GItem& it : h.s2.items) {
         if (it.cols > gather_digits_max_cols())
           throw Err{TT_ERR_INVALID_ARG, "exact split: a sector longer than " + std::to_string(gather_digits_max_cols())};
+        // the digit gather stores column pairs (a BF16 pair per 32-bit word;
+        // an odd row's last pair ends in the row's zero padding)
+        if (((it.dst & 0x00FFFFFFFFFFFFFFull) | (uint64_t)it.dst_rs | (uint64_t)h.t2_size) & 1)
+          throw Err{TT_ERR_STATE, "S2 digit rows not at even BF16 offsets"};
+      }
     }
   }
 
@@ -522,7 +536,8 @@ struct Eng {
         upload(c, cp.gram[p], q.gram[p]);
         upload(c, cp.app[p], q.app[p]);
         for (const CholJob& J : cp.cj[p])
-          if (J.g + (int64_t)J.parts * J.n * J.n > wsz || J.parts < 1 || J.r + (int64_t)J.n * J.n > wsz || J.ri + (int64_t)J.n * J.n > wsz)
+          if (J.g + (int64_t)J.parts * J.n * J.n > wsz || J.parts < 1 || J.r + (int64_t)J.n * J.n > wsz ||
+              J.ri + (int64_t)J.n * J.n > wsz || J.pk < 0 || J.pk + (int64_t)J.n * (J.n + 1) / 2 > wsz)
             throw Err{TT_ERR_STATE, "Cholesky job outside the workspace"};
         q.ncj[p] = (int)cp.cj[p].size();
         q.maxn[p] = 0;
@@ -800,8 +815,10 @@ struct Eng {
     const long e = prof_begin(kind, g.d.flops);
     if (use_mixed) {
       launch_split(g, b, g.choice);
-    } else if (oz_now) {
+    } else if (f64_kernel == 1) {
       CK(launch_gemm_oz(g.d, b, st));
+    } else if (f64_kernel == 2) {
+      CK(launch_gemm_df(g.d, b, st));
     } else {
       CK(launch_gemm_f64(g.d, b, st));
     }
@@ -995,7 +1012,7 @@ struct Eng {
       gather(s.s2, b, 1, r->nsplit);
       gemm(s.s3l, b, true, 1);
     } else {
-      OzScope oz(*this, env_oz());
+      OzScope oz(*this, env_f64_kernel());
       b.p[S_X] = r->A[j].p;
       b.p[S_L] = r->L[j].p;
       gemm(s.s1, b, false, 1);
@@ -1026,7 +1043,7 @@ struct Eng {
       gather(s.r2, b, 1, r->nsplit);
       gemm(s.r3, b, true, 1);
     } else {
-      OzScope oz(*this, env_oz());
+      OzScope oz(*this, env_f64_kernel());
       b.p[S_X] = r->A[j].p;
       b.p[S_R] = r->R[j + 1].p;
       gemm(s.r1, b, false, 1);
@@ -1089,15 +1106,20 @@ struct Eng {
       return;
     }
     CK(cudaMemsetAsync(q.fail.p, 0, q.h.jobs.size() * sizeof(int), st));
+    // the mixed modes run the Gram and apply GEMMs in double-float on the
+    // FP32 pipe (their error budget is far above ~2^-46), FP64 mode in FP64
+    auto qr_gemm = [&](const DevGemmBuf& g) { CK(mixed() ? launch_gemm_df(g.d, b, st) : launch_gemm_f64(g.d, b, st)); };
     for (int p = 0; p < 3; ++p) {
       long e = prof_begin(11, q.gram[p].d.flops);
-      CK(launch_gemm_f64(q.gram[p].d, b, st));
+      qr_gemm(q.gram[p]);
       prof_end(e);
       e = prof_begin(12, 0);
-      CK(launch_chol_inv((const CholJob*)q.cjobs[p].p, q.ncj[p], dptr(r->ws), (int*)q.fail.p, st, q.maxn[p]));
+      // the mixed modes factorise in double-float (their error budget is far
+      // above ~2^-46), FP64 mode in FP64
+      CK(launch_chol_inv((const CholJob*)q.cjobs[p].p, q.ncj[p], dptr(r->ws), (int*)q.fail.p, st, q.maxn[p], mixed()));
       prof_end(e);
       e = prof_begin(11, q.app[p].d.flops);
-      CK(launch_gemm_f64(q.app[p].d, b, st));
+      qr_gemm(q.app[p]);
       prof_end(e);
       count(3);
     }
@@ -2330,7 +2352,7 @@ int growth_arith(int prec) { return prec == 3 ? 0 : prec; }
 bool valid_opts(const tt_run_opts* o) {
   return o && o->D_max >= 1 && o->krylov_dim >= 1 && o->krylov_dim <= 16 && o->precision >= 0 && o->precision <= 3 &&
          o->growth_precision >= -1 && o->growth_precision <= 3 && o->svd_cut >= 0 && o->degen_tol >= 0 &&
-         o->env_precision >= -1 && o->env_precision <= 1;
+         o->env_precision >= -1 && o->env_precision <= 2;
 }
 
 }  // namespace
@@ -2338,6 +2360,60 @@ bool valid_opts(const tt_run_opts* o) {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+namespace {
+
+// the statistics window: opened by the first step call after tt_stats_get
+void stats_open(tt_rho* rho, cudaStream_t st) {
+  if (rho->stats_pending) return;
+  rho->heff_flops_acc = rho->step_flops_acc = 0;
+  rho->launches_acc = 0;
+  rho->qr_sectors_acc = 0;
+  rho->evused = 0;
+  for (int k = 0; k < 13; ++k) { rho->kind_ms[k] = 0; rho->kind_n[k] = 0; rho->kind_flops[k] = 0; }
+  CK(cudaEventRecord(rho->ev0, st));
+}
+
+void count_replay(tt_rho* rho) {
+  rho->heff_flops_acc += rho->graph_heff_flops;
+  rho->step_flops_acc += rho->graph_step_flops;
+  rho->launches_acc += rho->graph_launches;
+  rho->qr_sectors_acc += rho->graph_qr_sectors;
+  ++rho->graph_replays;
+}
+
+void stats_close(tt_rho* rho, cudaStream_t st) {
+  CK(cudaEventRecord(rho->ev1, st));
+  rho->stats.heff_flops = rho->heff_flops_acc;
+  rho->stats.step_flops = rho->step_flops_acc;
+  rho->stats.launches = rho->launches_acc;
+  rho->stats.qr_sectors = rho->qr_sectors_acc;
+  rho->stats.n_sites = rho->N;
+  rho->stats_pending = true;
+}
+
+}  // namespace
+
+namespace tt {
+
+bool rho_graph_current(const tt_rho* rho, double dtau) {
+  return rho && rho->graph && rho->graph_tmpl && !rho->poisoned && !rho->prof && !rho->graph_prof &&
+         rho->graph_dtau == dtau && rho->graph_buf_gen == rho->ctx->buf_gen && rho->graph_wait_ns == rho->ctx->wait_ns;
+}
+
+void rho_account_replays(tt_rho* rho, double dtau, int n, cudaStream_t st, bool before) {
+  if (before) {
+    stats_open(rho, st);
+    return;
+  }
+  for (int i = 0; i < n; ++i) {
+    count_replay(rho);
+    rho->beta += dtau;
+  }
+  stats_close(rho, st);
+}
+
+}  // namespace tt
+
 extern "C" {
 
 tt_status tt_ctx_create(const tt_alloc_cb* alloc, void* cuda_stream, tt_ctx** out) {
@@ -2458,6 +2534,7 @@ void tt_rho_destroy(tt_rho* rho) {
   for (cudaEvent_t e : rho->evpool) cudaEventDestroy(e);
   for (cudaEvent_t e : rho->gpool) cudaEventDestroy(e);
   if (rho->graph) cudaGraphExecDestroy(rho->graph);
+  if (rho->graph_tmpl) cudaGraphDestroy(rho->graph_tmpl);
   if (rho->ev0) cudaEventDestroy(rho->ev0);
   if (rho->ev1) cudaEventDestroy(rho->ev1);
   free_rho(rho);
@@ -2507,14 +2584,7 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
     if (!rho->ev1) CK(cudaEventCreate(&rho->ev1));
     cudaStream_t st = rho->ctx->st;
     // statistics accumulate over the calls since the last tt_stats_get
-    if (!rho->stats_pending) {
-      rho->heff_flops_acc = rho->step_flops_acc = 0;
-      rho->launches_acc = 0;
-      rho->qr_sectors_acc = 0;
-      rho->evused = 0;
-      for (int k = 0; k < 13; ++k) { rho->kind_ms[k] = 0; rho->kind_n[k] = 0; rho->kind_flops[k] = 0; }
-      CK(cudaEventRecord(rho->ev0, st));
-    }
+    stats_open(rho, st);
     if (rho->graph && (rho->graph_dtau != dtau || rho->graph_prof != rho->prof ||
                        rho->graph_buf_gen != rho->ctx->buf_gen || rho->graph_wait_ns != rho->ctx->wait_ns))
       e.drop_graph();
@@ -2559,12 +2629,14 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
         throw Err{TT_ERR_CUDA, "capture of the beta-step failed"};
       }
       cudaError_t ie = cudaGraphInstantiate(&rho->graph, g, 0);
-      cudaGraphDestroy(g);
       if (ie != cudaSuccess) {
         cudaGetLastError();
+        cudaGraphDestroy(g);
         rho->graph = nullptr;
         throw Err{TT_ERR_CUDA, "graph instantiation failed"};
       }
+      rho->graph_tmpl = g;
+      ++rho->graph_gen;
       rho->graph_dtau = dtau;
       rho->graph_prof = rho->prof;
       rho->graph_wait_ns = rho->ctx->wait_ns;
@@ -2583,26 +2655,18 @@ tt_status tt_tdvp_step(tt_rho* rho, const tt_mpo* mpo, double dtau, int n_steps)
     for (; s < n_steps; ++s) {
       if (rho->graph) {
         CK(cudaGraphLaunch(rho->graph, st));
-        rho->heff_flops_acc += rho->graph_heff_flops;
-        rho->step_flops_acc += rho->graph_step_flops;
-        rho->launches_acc += rho->graph_launches;
-        rho->qr_sectors_acc += rho->graph_qr_sectors;
-        ++rho->graph_replays;
+        count_replay(rho);
       } else {
         e.sweep_lr(dtau / 4);
         e.sweep_rl(dtau / 4);
       }
       rho->beta += dtau;
     }
-    CK(cudaEventRecord(rho->ev1, st));
-    rho->stats.heff_flops = rho->heff_flops_acc;
-    rho->stats.step_flops = rho->step_flops_acc;
-    rho->stats.launches = rho->launches_acc;
-    rho->stats.qr_sectors = rho->qr_sectors_acc;
-    rho->stats.n_sites = rho->N;
-    rho->stats_pending = true;
+    stats_close(rho, st);
   });
 }
+
+
 
 tt_status tt_measure(tt_rho* rho, const tt_mpo* mpo, tt_obs* out) {
   if (!rho || mpo != rho->mpo || !out) return TT_ERR_INVALID_ARG;

@@ -180,6 +180,8 @@ struct tt_rho {
   bool prof = false;
   // CUDA graph of one beta-step (the block structure is fixed in 1-TDVP)
   cudaGraphExec_t graph = nullptr;
+  cudaGraph_t graph_tmpl = nullptr;       // the captured graph (a batch composes these)
+  unsigned long long graph_gen = 0;       // bumped whenever the graph is replaced or dropped
   double graph_dtau = 0.0;
   bool graph_prof = false;
   long long graph_wait_ns = 0;            // wait budget baked into the captured launches
@@ -203,3 +205,14 @@ struct tt_rho {
   long long qr_sectors_acc = 0, graph_qr_sectors = 0;
   long long tuned[tt::TK_N] = {0, 0, 0};  // plans per autotuned kernel choice
 };
+
+namespace tt {
+// Batch support (tt_batch.cu composes the instances' captured beta-step graphs
+// into one parent graph).  rho_graph_current: rho's captured step graph can be
+// replayed for dtau as it is (not profiling, nothing replaced since the
+// capture).  rho_account_replays: the host bookkeeping of n replays of that
+// graph launched elsewhere on stream st; call with before = true ahead of the
+// launches (opens the statistics window) and before = false after them.
+bool rho_graph_current(const tt_rho* rho, double dtau);
+void rho_account_replays(tt_rho* rho, double dtau, int n, cudaStream_t st, bool before);
+}  // namespace tt

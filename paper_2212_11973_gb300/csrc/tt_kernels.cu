@@ -27,7 +27,7 @@ __device__ __forceinline__ long long off_of(Ref r) { return (long long)(r & 0x00
 
 template <typename T>
 __device__ __forceinline__ T* rptr(const Bases& b, Ref r) {
-  return reinterpret_cast<T*>(b.p[slot_of(r)]) + off_of(r);
+  return reinterpret_cast<T*>(sel_base(b, slot_of(r))) + off_of(r);
 }
 
 constexpr int NBLK = 304;  // 2 x 152 SMs for the vector reductions
@@ -116,6 +116,97 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GGroup* __restrict_
 }
 
 // ---------------------------------------------------------------------------
+// The same grouped GEMM in double-float arithmetic on the FP32 pipe (GB300
+// issues ~2 FP64 FMA per clock per SM against 128 FP32): FP64 operands split
+// into float pairs (hi, lo) as they are staged, every product by the FMA
+// TwoProduct with the cross terms, every sum by TwoSum into an unnormalised
+// (hi, lo) accumulator (Dekker; Knuth TAOCP vol. 2, 4.2.2): ~2^-46 relative
+// per operation, K 2^-46 of sum |a| |b| per output.  Output FP64.  Used by the
+// mixed modes' CholeskyQR Gram and apply GEMMs.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_split(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+__global__ void __launch_bounds__(256) gemm_df_kernel(const GGroup* __restrict__ groups, const GSeg* __restrict__ segs,
+                                                      const GTile* __restrict__ tiles, Bases bs) {
+  __shared__ float2 As[FBK][FBM + 1];
+  __shared__ float2 Bs[FBK][FBN + 1];
+  const GTile tl = tiles[blockIdx.x];
+  const GGroup g = groups[tl.g];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  float ah_[4][4], al_[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { ah_[i][j] = 0.f; al_[i][j] = 0.f; }
+
+  for (int si = g.seg0; si < g.seg1; ++si) {
+    const GSeg sg = segs[si];
+    const double* A = rptr<const double>(bs, sg.A);
+    const double* B = rptr<const double>(bs, sg.B);
+    for (int k0 = 0; k0 < sg.K; k0 += FBK) {
+      for (int e = tid; e < FBM * FBK; e += 256) {
+        int mm, kk;
+        if (sg.tA) { mm = e % FBM; kk = e / FBM; } else { kk = e % FBK; mm = e / FBK; }
+        const int gm = tl.m0 + mm, gk = k0 + kk;
+        double v = 0.0;
+        if (gm < g.M && gk < sg.K) v = sg.tA ? A[(long long)gk * sg.lda + gm] : A[(long long)gm * sg.lda + gk];
+        As[kk][mm] = df_split(v);
+      }
+      for (int e = tid; e < FBN * FBK; e += 256) {
+        int nn, kk;
+        if (sg.tB) { kk = e % FBK; nn = e / FBK; } else { nn = e % FBN; kk = e / FBN; }
+        const int gn = tl.n0 + nn, gk = k0 + kk;
+        double v = 0.0;
+        if (gn < g.N && gk < sg.K) v = sg.tB ? B[(long long)gn * sg.ldb + gk] : B[(long long)gk * sg.ldb + gn];
+        Bs[kk][nn] = df_split(v);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < FBK; ++kk) {
+        float2 a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float p = a[i].x * b[j].x;
+            float e = fmaf(a[i].x, b[j].x, -p);
+            e = fmaf(a[i].x, b[j].y, e);
+            e = fmaf(a[i].y, b[j].x, e);
+            const float s = ah_[i][j] + p;
+            const float bp = s - ah_[i][j];
+            al_[i][j] += ((ah_[i][j] - (s - bp)) + (p - bp)) + e;
+            ah_[i][j] = s;
+          }
+      }
+      __syncthreads();
+    }
+  }
+  double* C = rptr<double>(bs, g.C);
+  const bool accum = g.flags & 1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = tl.m0 + ty + 16 * i;
+    if (gm >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = tl.n0 + tx + 16 * j;
+      if (gn >= g.N) continue;
+      double* c = C + (long long)gm * g.ldc + gn;
+      const double v = (double)ah_[i][j] + (double)al_[i][j];
+      *c = accum ? *c + v : v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Split-BF16 grouped GEMM on the tensor cores (mma.sync m16n8k16, FP32
 // accumulation).  Operands are stored as NS bf16 levels x = x0 + x1 (+ x2),
 // level l at element offset l * lo[slot]; the products with l_A + l_B < NS are
@@ -168,7 +259,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_split_kernel(const GGroup* __re
     const GSeg sg = segs[si];
     const __nv_bfloat16* A0 = rptr<const __nv_bfloat16>(bs, sg.A);
     const __nv_bfloat16* B0 = rptr<const __nv_bfloat16>(bs, sg.B);
-    const long long loA = bs.lo[slot_of(sg.A)], loB = bs.lo[slot_of(sg.B)];
+    const long long loA = sel_lo(bs, slot_of(sg.A)), loB = sel_lo(bs, slot_of(sg.B));
     for (int k0 = 0; k0 < sg.K; k0 += HBK) {
       for (int e = tid; e < HBM * HBK; e += 128) {
         int mm, kk;
@@ -297,7 +388,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GItem* __restrict__ i
         }
         if constexpr (OUT == 0) rptr<double>(bs, it.dst)[d] = acc;
         else if constexpr (OUT == 1) rptr<float>(bs, it.dst)[d] = (float)acc;
-        else store_split_f64<OUT>(rptr<__nv_bfloat16>(bs, it.dst) + d, bs.lo[slot_of(it.dst)], acc);
+        else store_split_f64<OUT>(rptr<__nv_bfloat16>(bs, it.dst) + d, sel_lo(bs, slot_of(it.dst)), acc);
       } else {
         float acc = 0.f;
         for (int k = it.c0; k < it.c1; ++k) {
@@ -306,7 +397,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const GItem* __restrict__ i
         }
         if constexpr (OUT == 0) rptr<double>(bs, it.dst)[d] = (double)acc;
         else if constexpr (OUT == 1) rptr<float>(bs, it.dst)[d] = acc;
-        else store_split_f32<OUT>(rptr<__nv_bfloat16>(bs, it.dst) + d, bs.lo[slot_of(it.dst)], acc);
+        else store_split_f32<OUT>(rptr<__nv_bfloat16>(bs, it.dst) + d, sel_lo(bs, slot_of(it.dst)), acc);
       }
     }
 }
@@ -350,7 +441,7 @@ __global__ void __launch_bounds__(256) tile_copy_kernel(const CItem* __restrict_
         const long long o = (long long)r * it.dst_rs + (long long)c * it.dst_cs;
         const double v = tile[lr][lc];
         if constexpr (NS == 0) rptr<double>(bs, it.dst)[o] = v;
-        else store_split_f64<NS>(rptr<__nv_bfloat16>(bs, it.dst) + o, bs.lo[slot_of(it.dst)], v);
+        else store_split_f64<NS>(rptr<__nv_bfloat16>(bs, it.dst) + o, sel_lo(bs, slot_of(it.dst)), v);
       }
     }
     __syncthreads();
@@ -734,22 +825,88 @@ __device__ __forceinline__ void qr_one(const QrJob J, double* __restrict__ ws) {
   }
 }
 
-// The same Cholesky + inverse with the matrix in shared memory: the upper
-// triangle packed row by row (row i holds columns i..n-1), factorised in
-// place (right-looking, a warp per trailing row, lanes along the columns),
-// R written out, then inverted in place column by column (LAPACK trti2 order:
-// column j of R^-1 = -R^-1(0:j, 0:j) R(0:j, j) / R(j, j), the product with the
-// already inverted leading block as a parallel triangular mat-vec).  Used when
-// every sector of the launch has n <= CHOL_SMEM_MAXN.
+// Cholesky G = R^T R (R upper; G the sum of the job's partial Gram matrices,
+// row-major n x n at ws + g) and R^-1, one CTA per job.  Optional diagonal
+// shift s = 11 (m n + n (n + 1)) u tr(G) (shifted CholeskyQR, Fukaya, Kannan,
+// Nakatsukasa, Yamamoto, Yanagisawa 2020).  A non-positive or non-finite pivot
+// marks fail[sec] and leaves the job to the Householder fallback.
+//
+// The upper triangle is packed row by row (row i holds columns i..n-1) in
+// shared memory, or for n > CHOL_SMEM_MAXN in the job's workspace scratch,
+// factorised in place (right-looking: pivot row scaled, then every trailing
+// row updated, a warp per row, lanes along the columns), R written out, then
+// inverted in place, also right-looking: rows k = n-1 .. 0 of R^-1 are
+// finalised in turn (row k divided by R(k, k)) and every row above takes its
+// rank-1 update, R^-1(i, c) -= R(i, k) R^-1(k, c) (back substitution of
+// R X = I, with R(i, k) read just before its slot becomes R^-1(i, k)).  Every
+// step is parallel over a whole trailing block.
+//
+// Element arithmetic: FP64, or double-float (a pair of floats, the error-free
+// TwoSum / FMA TwoProduct transformations of Dekker and Knuth; ~2^-46
+// relative), which runs on the FP32 pipe: GB300 executes ~2 FP64 FMA per clock
+// per SM against 128 FP32, and one CTA factorises one sector.
 constexpr int CHOL_SMEM_MAXN = 230;
+constexpr int CHOL_T = 512;
 
 __device__ __forceinline__ int pk(int i, int j, int n) { return i * n - (i * (i - 1)) / 2 + (j - i); }
 
-__global__ void __launch_bounds__(256) chol_inv_smem_kernel(const CholJob* __restrict__ jobs, double* __restrict__ ws,
-                                                            int* __restrict__ fail) {
-  extern __shared__ double sm[];
+struct CholF64 {
+  using T = double;
+  static constexpr double u = 1.1102230246251565e-16;  // unit roundoff 2^-53
+  static __device__ __forceinline__ T of(double x) { return x; }
+  static __device__ __forceinline__ double dbl(T a) { return a; }
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  // a - b c
+  static __device__ __forceinline__ T fnms(T a, T b, T c) { return fma(-b, c, a); }
+  static __device__ __forceinline__ T mul(T a, double s) { return a * s; }
+};
+
+struct CholDF {
+  using T = float2;  // value x + y, |y| <= ulp(x) / 2
+  // unit roundoff of the double-float Gram (gemm_df_kernel) and factor
+  static constexpr double u = 1.4210854715202004e-14;  // 2^-46
+  static __device__ __forceinline__ T of(double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  }
+  static __device__ __forceinline__ double dbl(T a) { return (double)a.x + (double)a.y; }
+  static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ T two_sum(float s, float t) {
+    const float h = s + t;
+    const float bp = h - s;
+    return make_float2(h, (s - (h - bp)) + (t - bp));
+  }
+  static __device__ __forceinline__ T fnms(T a, T b, T c) {
+    const float p = b.x * c.x;
+    float e = fmaf(b.x, c.x, -p);  // b.x c.x = p + e exactly
+    e = fmaf(b.x, c.y, e);
+    e = fmaf(b.y, c.x, e);
+    const float s = a.x - p;       // a.x - p = s + t exactly
+    const float bp = s - a.x;
+    float t = (a.x - (s - bp)) + (-p - bp);
+    t += a.y - e;
+    return two_sum(s, t);
+  }
+  static __device__ __forceinline__ T mul(T a, double v) {
+    const float sh = (float)v, sl = (float)(v - (double)sh);
+    const float p = a.x * sh;
+    float e = fmaf(a.x, sh, -p);
+    e = fmaf(a.x, sl, e);
+    e = fmaf(a.y, sh, e);
+    return two_sum(p, e);
+  }
+};
+
+template <class A>
+__global__ void __launch_bounds__(CHOL_T, 1) chol_inv_smem_kernel(const CholJob* __restrict__ jobs, double* __restrict__ ws,
+                                                               int* __restrict__ fail) {
+  using T = typename A::T;
+  extern __shared__ __align__(16) unsigned char chol_raw[];
   const CholJob J = jobs[blockIdx.x];
   const int n = J.n;
+  // the packed triangle: shared memory, or the job's workspace scratch (L2
+  // resident) for the sectors too large for it
+  T* sm = n <= CHOL_SMEM_MAXN ? reinterpret_cast<T*>(chol_raw) : reinterpret_cast<T*>(ws + J.pk);
   if (J.shift == 3) {
     if (threadIdx.x == 0) fail[J.sec] = 1;
     return;
@@ -758,10 +915,9 @@ __global__ void __launch_bounds__(256) chol_inv_smem_kernel(const CholJob* __res
   double* G = ws + J.g;
   double* R = ws + J.r;
   double* Ri = ws + J.ri;
-  double* tmp = sm + (n * (n + 1)) / 2;  // n doubles
   const long long nn = (long long)n * n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  __shared__ double piv, red[8];
+  __shared__ double piv, red[CHOL_T / 32];
   __shared__ int bad;
   // G = sum of the partial Gram matrices, upper triangle into shared memory
   for (int i = warp; i < n; i += nw)
@@ -769,7 +925,7 @@ __global__ void __launch_bounds__(256) chol_inv_smem_kernel(const CholJob* __res
       const long long e = (long long)i * n + j;
       double acc = G[e];
       for (int s = 1; s < J.parts; ++s) acc += G[s * nn + e];
-      sm[pk(i, j, n)] = acc;
+      sm[pk(i, j, n)] = A::of(acc);
     }
   __syncthreads();
   if (J.shift == 2) {
@@ -778,7 +934,7 @@ __global__ void __launch_bounds__(256) chol_inv_smem_kernel(const CholJob* __res
     double mx = 0.0;
     for (int i = warp; i < n; i += nw)
       for (int j = i + lane; j < n; j += 32) {
-        const double dev = fabs(sm[pk(i, j, n)] - (i == j ? 1.0 : 0.0));
+        const double dev = fabs(A::dbl(sm[pk(i, j, n)]) - (i == j ? 1.0 : 0.0));
         mx = (dev <= mx) ? mx : (dev == dev ? dev : 1e300);
       }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -797,11 +953,11 @@ __global__ void __launch_bounds__(256) chol_inv_smem_kernel(const CholJob* __res
           R[e] = 0.0;
           Ri[e] = 0.0;
         } else if (j == i) {
-          const double h = 0.5 * (sm[pk(i, i, n)] - 1.0);
+          const double h = 0.5 * (A::dbl(sm[pk(i, i, n)]) - 1.0);
           R[e] = 1.0 + h;
           Ri[e] = 1.0 - h;
         } else {
-          const double g = sm[pk(i, j, n)];
+          const double g = A::dbl(sm[pk(i, j, n)]);
           R[e] = g;
           Ri[e] = -g;
         }
@@ -812,17 +968,18 @@ __global__ void __launch_bounds__(256) chol_inv_smem_kernel(const CholJob* __res
   if (tid == 0) {
     bad = 0;
     if (J.shift == 1) {
-      // shift s = 11 (m n + n (n + 1)) u ||X||^2 with ||X||^2 <= tr(G)
+      // shift s = 11 (m n + n (n + 1)) u ||X||^2 with ||X||^2 <= tr(G), u the
+      // unit roundoff of the arithmetic that formed G and factorises it
       double tr = 0.0;
-      for (int i = 0; i < n; ++i) tr += sm[pk(i, i, n)];
-      const double sft = 11.0 * ((double)J.m * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * tr;
-      for (int i = 0; i < n; ++i) sm[pk(i, i, n)] += sft;
+      for (int i = 0; i < n; ++i) tr += A::dbl(sm[pk(i, i, n)]);
+      const double sft = 11.0 * ((double)J.m * n + (double)n * (n + 1)) * A::u * tr;
+      for (int i = 0; i < n; ++i) sm[pk(i, i, n)] = A::of(A::dbl(sm[pk(i, i, n)]) + sft);
     }
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (tid == 0) {
-      const double d = sm[pk(k, k, n)];
+      const double d = A::dbl(sm[pk(k, k, n)]);
       if (!(d > 0.0) || !isfinite(d)) {
         bad = 1;
         fail[J.sec] = 1;
@@ -831,37 +988,38 @@ __global__ void __launch_bounds__(256) chol_inv_smem_kernel(const CholJob* __res
     }
     __syncthreads();
     if (bad) return;
-    const double p = piv;
-    for (int j = k + tid; j < n; j += blockDim.x) sm[pk(k, j, n)] /= p;
+    const double p = piv, ip = 1.0 / p;
+    for (int j = k + tid; j < n; j += blockDim.x) sm[pk(k, j, n)] = j == k ? A::of(p) : A::mul(sm[pk(k, j, n)], ip);
     __syncthreads();
     for (int i = k + 1 + warp; i < n; i += nw) {
-      const double rki = sm[pk(k, i, n)];
-      for (int j = i + lane; j < n; j += 32) sm[pk(i, j, n)] -= rki * sm[pk(k, j, n)];
+      const T rki = sm[pk(k, i, n)];
+      for (int j = i + lane; j < n; j += 32) sm[pk(i, j, n)] = A::fnms(sm[pk(i, j, n)], rki, sm[pk(k, j, n)]);
     }
     __syncthreads();
   }
   for (long long e = tid; e < nn; e += blockDim.x) {
     const int i = (int)(e / n), j = (int)(e % n);
-    R[e] = (j >= i) ? sm[pk(i, j, n)] : 0.0;
+    R[e] = (j >= i) ? A::dbl(sm[pk(i, j, n)]) : 0.0;
+  }
+  // in-place inverse, rows from the bottom
+  for (int k = n - 1; k >= 0; --k) {
+    __syncthreads();
+    if (tid == 0) piv = 1.0 / A::dbl(sm[pk(k, k, n)]);
+    __syncthreads();
+    const double ik = piv;
+    for (int c = k + tid; c < n; c += blockDim.x) sm[pk(k, c, n)] = c == k ? A::of(ik) : A::mul(sm[pk(k, c, n)], ik);
+    __syncthreads();
+    for (int i = warp; i < k; i += nw) {
+      const T rik = sm[pk(i, k, n)];
+      __syncwarp();
+      for (int c = k + lane; c < n; c += 32)
+        sm[pk(i, c, n)] = A::fnms(c == k ? A::zero() : sm[pk(i, c, n)], rik, sm[pk(k, c, n)]);
+    }
   }
   __syncthreads();
-  // in-place inverse of the upper triangle, column by column
-  for (int j = 0; j < n; ++j) {
-    const double ajj = 1.0 / sm[pk(j, j, n)];
-    // tmp(0:j) = Rinv(0:j, 0:j) R(0:j, j), rows in parallel
-    for (int i = tid; i < j; i += blockDim.x) {
-      double acc = 0.0;
-      for (int q = i; q < j; ++q) acc = fma(sm[pk(i, q, n)], sm[pk(q, j, n)], acc);
-      tmp[i] = acc;
-    }
-    __syncthreads();
-    for (int i = tid; i < j; i += blockDim.x) sm[pk(i, j, n)] = -ajj * tmp[i];
-    if (tid == 0) sm[pk(j, j, n)] = ajj;
-    __syncthreads();
-  }
   for (long long e = tid; e < nn; e += blockDim.x) {
     const int i = (int)(e / n), j = (int)(e % n);
-    Ri[e] = (j >= i) ? sm[pk(i, j, n)] : 0.0;
+    Ri[e] = (j >= i) ? A::dbl(sm[pk(i, j, n)]) : 0.0;
   }
 }
 
@@ -949,6 +1107,12 @@ int lanczos_nblk() { return NBLK; }
 cudaError_t launch_gemm_f64(const DevGemm& g, const Bases& b, cudaStream_t s) {
   if (g.ntiles64 == 0) return cudaSuccess;
   gemm_f64_kernel<<<g.ntiles64, 256, 0, s>>>(g.groups, g.segs, g.tiles64, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_df(const DevGemm& g, const Bases& b, cudaStream_t s) {
+  if (g.ntiles64 == 0) return cudaSuccess;
+  gemm_df_kernel<<<g.ntiles64, 256, 0, s>>>(g.groups, g.segs, g.tiles64, b);
   return cudaGetLastError();
 }
 
@@ -1079,135 +1243,20 @@ cudaError_t launch_qr_masked(const QrJob* jobs, int njobs, double* ws, const int
   return cudaGetLastError();
 }
 
-// Cholesky G = R^T R (R upper, G row-major n x n at ws + g) and R^-1, one CTA
-// per job.  Optional diagonal shift s = 11 (m n + n (n + 1)) u tr(G) (shifted
-// CholeskyQR, Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020).  A
-// non-positive or non-finite pivot marks fail[sec] and leaves the job to the
-// Householder fallback.
-__global__ void __launch_bounds__(256) chol_inv_kernel(const CholJob* __restrict__ jobs, double* __restrict__ ws,
-                                                       int* __restrict__ fail) {
-  const CholJob J = jobs[blockIdx.x];
-  const int n = J.n;
-  if (J.shift == 3) {  // more columns than rows: left to the Householder kernel
-    if (threadIdx.x == 0) fail[J.sec] = 1;
-    return;
-  }
-  if (fail[J.sec]) return;  // an earlier pass already gave up on this sector
-  double* G = ws + J.g;
-  double* R = ws + J.r;
-  double* Ri = ws + J.ri;
-  const long long nn = (long long)n * n;
-  __shared__ double piv, red[8];
-  __shared__ int bad;
-  // G = sum of the partial Gram matrices (upper triangle only is used)
-  if (J.parts > 1)
-    for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
-      if (e % n < e / n) continue;
-      double acc = G[e];
-      for (int s = 1; s < J.parts; ++s) acc += G[s * nn + e];
-      G[e] = acc;
-    }
-  __syncthreads();
-  if (J.shift == 2) {
-    // Last pass: G = I + E with E small.  Far from the identity means the
-    // earlier passes met a numerically rank-deficient block: Householder
-    // fallback.  When n max|E| <= 1e-8 the factor is I + F to first order,
-    // F = strict upper part of E + diag(E) / 2, and its inverse I - F; the
-    // neglected terms are O(|E|^2), below FP64 rounding.
-    double mx = 0.0;
-    for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
-      const int i = (int)(e / n), j = (int)(e % n);
-      if (j < i) continue;
-      const double dev = fabs(G[e] - (i == j ? 1.0 : 0.0));
-      mx = (dev <= mx) ? mx : (dev == dev ? dev : 1e300);
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    double all = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) all = fmax(all, red[q]);
-    if (!(all <= 1e-3)) {
-      if (threadIdx.x == 0) fail[J.sec] = 1;
-      return;
-    }
-    if ((double)n * all <= 1e-8) {
-      for (long long e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int i = (int)(e / n), j = (int)(e % n);
-        if (j < i) {
-          R[e] = 0.0;
-          Ri[e] = 0.0;
-        } else if (j == i) {
-          const double h = 0.5 * (G[e] - 1.0);
-          R[e] = 1.0 + h;
-          Ri[e] = 1.0 - h;
-        } else {
-          R[e] = G[e];
-          Ri[e] = -G[e];
-        }
-      }
-      return;
-    }
-  }
-  if (threadIdx.x == 0) {
-    bad = 0;
-    if (J.shift == 1) {
-      // shift s = 11 (m n + n (n + 1)) u ||X||^2 with ||X||^2 <= tr(G)
-      // (shifted CholeskyQR, Fukaya, Kannan, Nakatsukasa, Yamamoto, Yanagisawa 2020)
-      double tr = 0.0;
-      for (int i = 0; i < n; ++i) tr += G[(long long)i * n + i];
-      const double sft = 11.0 * ((double)J.m * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * tr;
-      for (int i = 0; i < n; ++i) G[(long long)i * n + i] += sft;
-    }
-  }
-  __syncthreads();
-  for (long long e = threadIdx.x; e < nn; e += blockDim.x) R[e] = 0.0;
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = G[(long long)k * n + k];
-      if (!(d > 0.0) || !isfinite(d)) {
-        bad = 1;
-        fail[J.sec] = 1;
-      }
-      piv = bad ? 1.0 : sqrt(d);
-    }
-    __syncthreads();
-    if (bad) return;
-    const double p = piv;
-    for (int j = k + threadIdx.x; j < n; j += blockDim.x) R[(long long)k * n + j] = G[(long long)k * n + j] / p;
-    __syncthreads();
-    const int w = n - k - 1;  // trailing upper triangle (i, j), k < i <= j
-    for (long long e = threadIdx.x; e < (long long)w * w; e += blockDim.x) {
-      const int i = k + 1 + (int)(e / w), j = k + 1 + (int)(e % w);
-      if (j >= i) G[(long long)i * n + j] -= R[(long long)k * n + i] * R[(long long)k * n + j];
-    }
-    __syncthreads();
-  }
-  // R^-1 (upper), one column per thread: R x = e_j by back substitution
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    for (int i = j + 1; i < n; ++i) Ri[(long long)i * n + j] = 0.0;
-    Ri[(long long)j * n + j] = 1.0 / R[(long long)j * n + j];
-    for (int i = j - 1; i >= 0; --i) {
-      double acc = 0.0;
-      for (int q = i + 1; q <= j; ++q) acc = fma(R[(long long)i * n + q], Ri[(long long)q * n + j], acc);
-      Ri[(long long)i * n + j] = -acc / R[(long long)i * n + i];
-    }
-  }
-}
-
-cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s, int maxn) {
+cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s, int maxn, bool df) {
   if (njobs == 0) return cudaSuccess;
-  if (maxn > 0 && maxn <= CHOL_SMEM_MAXN) {
-    const size_t smem = ((size_t)maxn * (maxn + 1) / 2 + maxn) * sizeof(double);
-    // once per process (thread-safe static initialisation): the largest size
-    static const cudaError_t e = cudaFuncSetAttribute(
-        chol_inv_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)(((size_t)CHOL_SMEM_MAXN * (CHOL_SMEM_MAXN + 1) / 2 + CHOL_SMEM_MAXN) * sizeof(double)));
-    if (e != cudaSuccess) return e;
-    chol_inv_smem_kernel<<<njobs, 256, smem, s>>>(jobs, ws, fail);
-    return cudaGetLastError();
-  }
-  chol_inv_kernel<<<njobs, 256, 0, s>>>(jobs, ws, fail);
+  const int ns = maxn < CHOL_SMEM_MAXN ? maxn : CHOL_SMEM_MAXN;
+  const size_t smem = ((size_t)ns * (ns + 1) / 2) * 8;
+  const int smax = (int)(((size_t)CHOL_SMEM_MAXN * (CHOL_SMEM_MAXN + 1) / 2) * 8);
+  // once per process (thread-safe static initialisation): the largest size
+  static const cudaError_t e1 =
+      cudaFuncSetAttribute(chol_inv_smem_kernel<CholF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  static const cudaError_t e2 =
+      cudaFuncSetAttribute(chol_inv_smem_kernel<CholDF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+  if (e1 != cudaSuccess) return e1;
+  if (e2 != cudaSuccess) return e2;
+  if (df) chol_inv_smem_kernel<CholDF><<<njobs, CHOL_T, smem, s>>>(jobs, ws, fail);
+  else chol_inv_smem_kernel<CholF64><<<njobs, CHOL_T, smem, s>>>(jobs, ws, fail);
   return cudaGetLastError();
 }
 

@@ -16,6 +16,25 @@ struct Bases {
   long long lo[8];
 };
 
+#ifdef __CUDACC__
+// bs.p[slot] by selects: indexing the by-value kernel argument with a
+// run-time slot would copy the array to local memory first
+__device__ __forceinline__ void* sel_base(const Bases& bs, int slot) {
+  void* p = bs.p[0];
+#pragma unroll
+  for (int k = 1; k < 8; ++k)
+    if (slot == k) p = bs.p[k];
+  return p;
+}
+__device__ __forceinline__ long long sel_lo(const Bases& bs, int slot) {
+  long long v = bs.lo[0];
+#pragma unroll
+  for (int k = 1; k < 8; ++k)
+    if (slot == k) v = bs.lo[k];
+  return v;
+}
+#endif
+
 // Device copies of a plan.
 struct DevGemm {
   GGroup* groups = nullptr;
@@ -66,6 +85,8 @@ struct RhoScalars {
 };
 
 cudaError_t launch_gemm_f64(const DevGemm& g, const Bases& b, cudaStream_t s);
+// The same in double-float arithmetic on the FP32 pipe (~2^-46 per operation).
+cudaError_t launch_gemm_df(const DevGemm& g, const Bases& b, cudaStream_t s);
 // Exact-accumulation split GEMM (tt_ozaki.cu): FP64 operands of the FP64
 // plans, four fixed-point BF16 digits per K tile, ~2^-32 normwise.
 cudaError_t launch_gemm_oz(const DevGemm& g, const Bases& b, cudaStream_t s);
@@ -135,8 +156,10 @@ cudaError_t launch_qr_job(const QrJob& job, double* ws, cudaStream_t s);
 cudaError_t launch_qr_masked(const QrJob* jobs, int njobs, double* ws, const int* only, int* nrun, cudaStream_t s);
 // Cholesky + triangular inverse per job (shifted on request); fail[sec] set on
 // a non-positive pivot.
-// maxn: the largest n of the jobs (shared-memory variant up to 230).
-cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s, int maxn = 0);
+// maxn: the largest n of the jobs (shared-memory variant up to 230); df: that
+// variant in double-float arithmetic (~2^-46) instead of FP64.
+cudaError_t launch_chol_inv(const CholJob* jobs, int njobs, double* ws, int* fail, cudaStream_t s, int maxn = 0,
+                            bool df = false);
 // Sign fix diag(R) >= 0 done inside launch_qr.
 
 // Per-block item of the local measurement (d = 4 local space, <= 4 pairs).

@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(OT) gemm_oz_kernel(const GGroup* __restrict__ 
 
   for (int si = g.seg0; si < g.seg1; ++si) {
     const GSeg sg = segs[si];
-    const double* A = reinterpret_cast<const double*>(bs.p[slot_of(sg.A)]) + off_of(sg.A);
-    const double* B = reinterpret_cast<const double*>(bs.p[slot_of(sg.B)]) + off_of(sg.B);
+    const double* A = reinterpret_cast<const double*>(sel_base(bs, slot_of(sg.A))) + off_of(sg.A);
+    const double* B = reinterpret_cast<const double*>(sel_base(bs, slot_of(sg.B))) + off_of(sg.B);
     for (int k0 = 0; k0 < sg.K; k0 += OBK) {
       double va[OEL], vb[OEL];
       const bool ka = sg.tA == 0, kb = sg.tB == 1;
@@ -231,10 +231,10 @@ __global__ void __launch_bounds__(OT) gemm_oz_kernel(const GGroup* __restrict__ 
       const long long o = (long long)gm * g.ldc + gn;
       const double v = (double)hi[j][r] + (double)lo[j][r];
       if (out_f32) {
-        float* C = reinterpret_cast<float*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+        float* C = reinterpret_cast<float*>(sel_base(bs, slot_of(g.C))) + off_of(g.C) + o;
         *C = accum ? *C + (float)v : (float)v;
       } else {
-        double* C = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+        double* C = reinterpret_cast<double*>(sel_base(bs, slot_of(g.C))) + off_of(g.C) + o;
         *C = accum ? *C + v : v;
       }
     }

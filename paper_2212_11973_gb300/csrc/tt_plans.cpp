@@ -558,7 +558,8 @@ CholQrPlan build_cholqr(const std::vector<QrJob>& jobs, int64_t ws0) {
         }
       }
       const int shift = p == 0 ? 1 : (p == 2 ? 2 : 0);
-      P.cj[p].push_back(CholJob{g, R[p], RI[p], m, n, shift, (int)sec, parts});
+      // the T region is free until the passes are done: packed scratch
+      P.cj[p].push_back(CholJob{g, R[p], RI[p], m, n, shift, (int)sec, parts, tt});
       for (int r0b = 0; r0b < n; r0b += RB) {
         P.app[p].add_group(std::min(RB, n - r0b), m, mkref(S_AUX2, Xo[p] + (int64_t)r0b * m), m, 0);
         P.app[p].add_seg(mkref(S_AUX2, RI[p] + r0b), n, 1, mkref(S_AUX2, X[p]), m, 0, std::min(n, r0b + RB));

@@ -240,11 +240,11 @@ __global__ void __launch_bounds__(128, 1) gemm_tc_kernel(const GGroup* __restric
         if (row < g.M && col < g.N) {
           const long long o = (long long)row * g.ldc + col;
           if (out_f32) {
-            float* C = reinterpret_cast<float*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+            float* C = reinterpret_cast<float*>(sel_base(bs, slot_of(g.C))) + off_of(g.C) + o;
             const float val = stg[rr * 33 + lane];
             *C = accum ? *C + val : val;
           } else {
-            double* C = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+            double* C = reinterpret_cast<double*>(sel_base(bs, slot_of(g.C))) + off_of(g.C) + o;
             const double val = stgd[rr * 33 + lane];
             *C = accum ? *C + val : val;
           }

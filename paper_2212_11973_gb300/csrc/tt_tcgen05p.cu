@@ -264,12 +264,12 @@ __global__ void __launch_bounds__(PTHREADS, 1) gemm_tcp_kernel(const GGroup* __r
           const long long o = (long long)row * g.ldc + tl.n0 + cb;
           const int ncol = min(32, g.N - tl.n0 - cb);
           if (out_f32) {
-            float* Cp = reinterpret_cast<float*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+            float* Cp = reinterpret_cast<float*>(sel_base(bs, slot_of(g.C))) + off_of(g.C) + o;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
               if (i < ncol) Cp[i] = accum ? Cp[i] + (h[i] + w[i]) : (h[i] + w[i]);
           } else {
-            double* Cp = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
+            double* Cp = reinterpret_cast<double*>(sel_base(bs, slot_of(g.C))) + off_of(g.C) + o;
 #pragma unroll
             for (int i = 0; i < 32; ++i)
               if (i < ncol) {

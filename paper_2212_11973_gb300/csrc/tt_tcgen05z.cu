@@ -18,11 +18,13 @@
 // 128 x 64 output tiles; warp 0 streams the digit tiles (A 4 x 16 KB, B 4 x
 // 8 KB per 64-wide K chunk) into two shared-memory stages, warp 1 issues the
 // MMAs of a segment into one of two TMEM buffers (4 accumulators x 64
-// columns each), warps 2-5 fold a finished buffer while the next segment's
-// MMAs run in the other, and write each finished tile as FP64 or as a two-
-// float pair (flags bit 1) through a shared-memory staging buffer (coalesced
-// row stores).  Waits are bounded as in the other tcgen05
-// kernels.
+// columns each), warps 2-9 fold a finished buffer while the next segment's
+// MMAs run in the other (two warps per TMEM lane quarter, 32 columns each,
+// so that every SM sub-partition has two folding warps), and write each
+// finished tile as FP64 or as a two-float pair (flags bit 1) through a
+// per-warp, XOR-swizzled shared-memory staging buffer (coalesced 128-byte
+// row stores, no cross-warp barrier).  Waits are bounded as in the other
+// tcgen05 kernels.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -44,11 +46,13 @@ constexpr int ZB_BYTES = ZBN * ZBK * 2;  // 8 KB per digit level
 constexpr int ZSTAGE_BYTES = ZDIG * (ZA_BYTES + ZB_BYTES);
 constexpr int ZSTAGES = 2;
 constexpr uint32_t ZTMEM_COLS = 512;
-constexpr int ZTHREADS = 192;
+constexpr int ZEPI = 8;  // epilogue warps
+constexpr int ZTHREADS = 64 + 32 * ZEPI;
 constexpr int ZMAXK = 256;  // longest segment whose digit sums stay exact
-// epilogue staging: 128 rows x 32 columns of 8-byte outputs (33-word rows
-// against bank conflicts), after the two TMA stages
-constexpr int ZSTG_BYTES = ZBM * 33 * 8;
+// epilogue staging, after the two TMA stages: per epilogue warp 32 rows x 16
+// columns of 8-byte outputs, column c of row r at word r * 16 + (c ^ (r & 15))
+constexpr int ZSTG_WARP = 32 * 16;
+constexpr int ZSTG_BYTES = ZEPI * ZSTG_WARP * 8;
 
 __device__ __forceinline__ void mbar_arrive_z(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -69,20 +73,30 @@ __device__ __forceinline__ bool wait_z(uint64_t* bar, uint32_t parity, long long
   }
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// 16 TMEM columns of this warp's lane quarter, not yet waited for: the caller
+// issues tmem_wait_ld16() with one set of registers and tmem_dep16() with
+// every other set before reading them (the registers pass through those asm
+// statements, so no use is scheduled before the wait)
+__device__ __forceinline__ void tmem_ld16_nw(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
-
-__device__ __forceinline__ float pow2z(int x) {
-  return (x >= -126 && x <= 127) ? __int_as_float((x + 127) << 23) : 0.f;
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void tmem_dep16(uint32_t* r) {
+  asm volatile(""
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 __device__ __forceinline__ void two_sum_z(float& hi, float& lo, float x) {
@@ -96,10 +110,9 @@ __device__ __forceinline__ void two_sum_z(float& hi, float& lo, float x) {
 // digit pair p -> (s, t): d = s + t ascending, the first pair of each d at
 // p = 0, 1, 3, 6
 __device__ __forceinline__ void pair_of(int p, int& s, int& t) {
-  const int ps[ZPAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
-  const int pt[ZPAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0};
-  s = ps[p];
-  t = pt[p];
+  const int d = (p >= 1) + (p >= 3) + (p >= 6);
+  s = p - d * (d + 1) / 2;
+  t = d - s;
 }
 
 __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __restrict__ groups,
@@ -110,7 +123,7 @@ __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __r
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[ZSTAGES], empty_bar[ZSTAGES], accf[2], acce[2];
   __shared__ uint32_t tmem_base_s;
-  __shared__ int abort_s, issued_s, consumed_s, last_commit_s, last_accf_s, epi_fail_s;
+  __shared__ int abort_s, issued_s, consumed_s, last_commit_s, last_accf_s;
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   volatile int* abort_f = &abort_s;
 
@@ -128,14 +141,13 @@ __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __r
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 4);
+      mbar_init(&acce[b], ZEPI);
     }
     abort_s = 0;
     issued_s = 0;
     consumed_s = 0;
     last_commit_s = -1;
     last_accf_s = -1;
-    epi_fail_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_before();
@@ -227,40 +239,66 @@ __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __r
     }
   } else {
     // ---------------- epilogue: fold per segment, write per tile ----------------
-    const int q = warp & 3;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (the quarter its SM sub-
+    // partition may access) and folds columns 32 h .. 32 h + 31 of them
+    const int q = warp & 3, h = (warp - 2) >> 2;
     const uint32_t lane_off = (uint32_t)(32 * q) << 16;
+    uint64_t* stg = reinterpret_cast<uint64_t*>(smem + ZSTAGES * ZSTAGE_BYTES) + (warp - 2) * ZSTG_WARP;
     int fg = 0;
     bool ok = true;
-    float hi[ZBN], lo[ZBN], dv[ZDIG][16];
+    float hi[32], lo[32];
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       const GTile tl = tiles[t];
       const GGroup g = groups[tl.g];
       const int row = tl.m0 + 32 * q + lane;
+      const int col_l = tl.n0 + 32 * h + lane;  // the column whose exponent this lane loads
 #pragma unroll
-      for (int i = 0; i < ZBN; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
+      for (int i = 0; i < 32; ++i) { hi[i] = 0.f; lo[i] = 0.f; }
       for (int si = g.seg0; si < g.seg1; ++si) {
         const GSeg sg = segs[si];
         const int b = fg & 1;
         ok = __all_sync(0xffffffffu, wait_z(&accf[b], (fg >> 1) & 1, wait_ns, abort_f, err));
         if (!ok) break;
         fence_after();
-        const int ea = row < g.M
-                           ? (int)reinterpret_cast<const short*>(bs.p[slot_of(sg.eA)])[off_of(sg.eA) + (long long)row * sg.eas]
-                           : 0;
-        const short* eBp = reinterpret_cast<const short*>(bs.p[slot_of(sg.eB)]) + off_of(sg.eB);
-        const uint32_t tb = tmem + 256 * b;
+        // the scale of D_0 at (row, column) is 2^(eA + eB - 2060): as a biased
+        // FP32 exponent xa + eB, clamped to [0, 254] (0: below the normal
+        // range, dropped like the digits below it)
+        const short* eAp = reinterpret_cast<const short*>(sel_base(bs, slot_of(sg.eA))) + off_of(sg.eA);
+        const short* eBp = reinterpret_cast<const short*>(sel_base(bs, slot_of(sg.eB))) + off_of(sg.eB);
+        const int ea = row < g.M ? (int)eAp[(long long)row * sg.eas] : 0;
+        const int eb = col_l < g.N ? (int)eBp[(long long)col_l * sg.ebs] : 0;
+        const int xa = ea - 2060 + 127;
+        const uint32_t tb = tmem + 256 * b + lane_off + 32 * h;
+        const bool first = si == g.seg0;
 #pragma unroll
-        for (int cb = 0; cb < ZBN; cb += 16) {
+        for (int cb = 0; cb < 32; cb += 16) {
+          uint32_t dv[ZDIG][16];
 #pragma unroll
-          for (int d = 0; d < ZDIG; ++d) tmem_ld16(tb + 64 * d + lane_off + cb, dv[d]);
+          for (int d = 0; d < ZDIG; ++d) tmem_ld16_nw(tb + 64 * d + cb, dv[d]);
+          tmem_wait_ld16(dv[0]);
+#pragma unroll
+          for (int d = 1; d < ZDIG; ++d) tmem_dep16(dv[d]);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const int col = tl.n0 + cb + i;
-            const int eb = col < g.N ? (int)eBp[(long long)col * sg.ebs] : 0;
-            const int x = ea + eb - 2060;
-            two_sum_z(hi[cb + i], lo[cb + i], dv[0][i] * pow2z(x));
-            two_sum_z(hi[cb + i], lo[cb + i], dv[1][i] * pow2z(x - 8));
-            lo[cb + i] += dv[2][i] * pow2z(x - 16) + dv[3][i] * pow2z(x - 24);
+            const int xe = xa + __shfl_sync(0xffffffffu, eb, cb + i);
+            const float sc = __int_as_float(min(max(xe, 0), 254) << 23);
+            // D_0 + D_1 2^-8 as an exact pair (sv, ev) (TwoSum), D_2 2^-16 and
+            // D_3 2^-24 into ev, then the pair scaled by the power of two sc
+            const float d0 = __uint_as_float(dv[0][i]);
+            const float p1 = __uint_as_float(dv[1][i]) * 0.00390625f;
+            const float sv = d0 + p1;
+            const float bp = sv - d0;
+            float ev = (d0 - (sv - bp)) + (p1 - bp);
+            ev = fmaf(__uint_as_float(dv[2][i]), 1.52587890625e-05f, ev);
+            ev = fmaf(__uint_as_float(dv[3][i]), 5.9604644775390625e-08f, ev);
+            const float s2 = sv * sc, e2 = ev * sc;
+            if (first) {
+              hi[cb + i] = s2;
+              lo[cb + i] = e2;
+            } else {
+              two_sum_z(hi[cb + i], lo[cb + i], s2);
+              lo[cb + i] += e2;
+            }
           }
         }
         fence_before();
@@ -268,52 +306,44 @@ __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __r
         if (lane == 0) mbar_arrive_z(&acce[b]);
         ++fg;
       }
-      // the four epilogue warps agree before the staging barriers: a warp that
-      // gave up (abort) still arrives here, and then all of them leave
-      if (lane == 0 && !ok) atomicExch(&epi_fail_s, 1);
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      if (*reinterpret_cast<volatile int*>(&epi_fail_s)) {
-        ok = false;
-        break;
-      }
-      // the finished tile through shared memory, 32 columns at a time, so that
-      // a warp stores 32 consecutive columns of one row per instruction
-      {
-        const bool accum = g.flags & 1, out_pair = g.flags & 2;
-        uint64_t* stg = reinterpret_cast<uint64_t*>(smem + ZSTAGES * ZSTAGE_BYTES);
-        const int r_loc = 32 * q + lane;
-        const int ncol = min(ZBN, g.N - tl.n0);
+      if (!ok) break;
+      // the finished 32 x 32 block, 16 columns at a time through this warp's
+      // staging buffer: one row per lane on the way in, 16 lanes per row (128
+      // contiguous bytes) on the way out
+      const bool accum = g.flags & 1, out_pair = g.flags & 2;
+      const int c_l = lane & 15;
+      uint64_t* const Cb = reinterpret_cast<uint64_t*>(sel_base(bs, slot_of(g.C))) + off_of(g.C);
 #pragma unroll
-        for (int h2 = 0; h2 < ZBN; h2 += 32) {
+      for (int cb = 0; cb < 32; cb += 16) {
+        // two separate loops: a select inside one would run the FP64
+        // conversions (GB300: ~2 per clock per SM) for pair outputs too
+        if (out_pair) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            uint64_t bits;
-            if (out_pair) {
-              const float2 v = make_float2(hi[h2 + i], lo[h2 + i]);
-              bits = *reinterpret_cast<const uint64_t*>(&v);
-            } else {
-              bits = (uint64_t)__double_as_longlong((double)hi[h2 + i] + (double)lo[h2 + i]);
-            }
-            stg[r_loc * 33 + i] = bits;
-          }
-          asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
-          const int col = h2 + lane;
-          for (int rr = warp - 2; rr < ZBM; rr += 4) {
-            const int grow = tl.m0 + rr;
-            if (grow < g.M && col < ncol) {
-              const long long o = (long long)grow * g.ldc + tl.n0 + col;
-              const uint64_t bits = stg[rr * 33 + lane];
-              if (out_pair) {
-                reinterpret_cast<uint64_t*>(reinterpret_cast<float2*>(bs.p[slot_of(g.C)]) + off_of(g.C))[o] = bits;
-              } else {
-                double* Cp = reinterpret_cast<double*>(bs.p[slot_of(g.C)]) + off_of(g.C) + o;
-                const double v = __longlong_as_double((long long)bits);
-                *Cp = accum ? *Cp + v : v;
-              }
-            }
-          }
-          asm volatile("bar.sync 1, 128;" ::: "memory");
+          for (int i = 0; i < 16; ++i)
+            stg[lane * 16 + (i ^ (lane & 15))] =
+                ((uint64_t)__float_as_uint(lo[cb + i]) << 32) | (uint64_t)__float_as_uint(hi[cb + i]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            stg[lane * 16 + (i ^ (lane & 15))] =
+                (uint64_t)__double_as_longlong((double)hi[cb + i] + (double)lo[cb + i]);
         }
+        __syncwarp();
+        const int col = tl.n0 + 32 * h + cb + c_l;
+        for (int rr = lane >> 4; rr < 32; rr += 2) {
+          const int grow = tl.m0 + 32 * q + rr;
+          if (grow < g.M && col < g.N) {
+            const long long o = (long long)grow * g.ldc + col;
+            const uint64_t bits = stg[rr * 16 + (c_l ^ (rr & 15))];
+            if (out_pair || !accum) {
+              Cb[o] = bits;
+            } else {
+              double* Cp = reinterpret_cast<double*>(Cb + o);
+              *Cp += __longlong_as_double((long long)bits);
+            }
+          }
+        }
+        __syncwarp();
       }
     }
   }
