@@ -410,6 +410,8 @@ def main():
     ap.add_argument("--env-precision", type=int, default=0, choices=[-1, 0, 1, 2],
                     help="tt_run_opts.env_precision of the mixed run (0: exact split, 2: double-float)")
     ap.add_argument("--save", default=None, help="write the prepared state (checkpoint) to this path")
+    ap.add_argument("--load", default=None,
+                    help="start from a checkpoint written by --save (same workload) instead of growing one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the mixed-vs-FP64 window and the FP64 timing from a shared checkpoint")
@@ -455,11 +457,14 @@ def main():
         mpo = tt.Mpo(ctx, cfg.Lx, cfg.Wy, cfg.periodic, t=cfg.t, U=cfg.U, mu=cfg.mu, form=cfg.form)
         t_prep = time.perf_counter()
         gD = min(args.grow_D, D)
-        rho = tt.Rho(ctx, mpo, cfg.beta0, tt.run_opts(gD, cfg.krylov, prec, growth_precision=prec,
-                                                      env_precision=args.env_precision))
-        rho.grow(cfg.dtau, 1.0)
-        if gD < D:
-            rho.pad(D)
+        if args.load:
+            rho = tt.Rho.load(ctx, mpo, args.load, tt.run_opts(D, cfg.krylov, prec, env_precision=args.env_precision))
+        else:
+            rho = tt.Rho(ctx, mpo, cfg.beta0, tt.run_opts(gD, cfg.krylov, prec, growth_precision=prec,
+                                                          env_precision=args.env_precision))
+            rho.grow(cfg.dtau, 1.0)
+            if gD < D:
+                rho.pad(D)
         for _ in range(args.warmup):
             rho.step(cfg.dtau, 1)
         torch.cuda.synchronize()
@@ -581,7 +586,9 @@ def main():
         "config": {"workload": cfg.name, "N": cfg.N, "D": D, "max_bond": max(dims), "dtau": cfg.dtau,
                    "krylov": cfg.krylov, "U": cfg.U, "mu": cfg.mu, "parallelism": f"replicas x{world}",
                    "env_precision": args.env_precision,
-                   "prep": f"2-TDVP growth at D={gD}, padded to D={D}, {args.warmup} warm-up steps ({t_prep:.1f} s)",
+                   "prep": (f"checkpoint of a 2-TDVP growth at D={gD} padded to D={D}, " if args.load else
+                            f"2-TDVP growth at D={gD}, padded to D={D}, ") +
+                           f"{args.warmup} warm-up steps ({t_prep:.1f} s)",
                    "l2": "state larger than L2 (no flush)"},
         "heff_tflops": heff_tflops, "env_tflops": (env_fl / (env_ms / 1e3) / 1e12) if env_ms > 0 else None,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 56,

@@ -321,7 +321,10 @@ def build_envs(st: State):
 
 
 # ----------------------------------------------------------------------------
-# 1-TDVP (Supplement, "Procedure of 1-TDVP", steps 1-7)
+# 1-TDVP: the one-site projector-splitting integrator of the tangent-space
+# evolution (Supplement, "Procedure of 1-TDVP"): every site is evolved forward
+# with its effective Hamiltonian, and between neighbouring sites the bond
+# matrix of the gauge move is evolved backward with the zero-site one
 # ----------------------------------------------------------------------------
 
 def _site_exp(st: State, j: int, t: float, K: int):

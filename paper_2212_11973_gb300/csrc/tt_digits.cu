@@ -133,7 +133,7 @@ __device__ __forceinline__ void df_fma(float& sh, float& sl, float ch, float cl,
 }
 
 constexpr int GMAXC = 256;  // longest digit row (segment) of the exact path
-constexpr int GMAXK = 64;   // MPO coefficients of an item split in shared memory
+constexpr int GMAXK = 64;   // most MPO coefficients of one item (split in shared memory)
 
 // Balanced base-256 digits of round(S + Sl) (a normalised two-float value,
 // |Sl| <= ulp(S) / 2, |S| < 2^31, scaled so that the row's bound is 2^31), in
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(DT) gather_digits_kernel(const GItem* __restri
   // arithmetic runs at ~1/64 of FP32 on GB300)
   __shared__ float2 cf[GMAXK];
   const int nk = it.c1 - it.c0;
-  for (int k = threadIdx.x; k < nk && k < GMAXK; k += DT) {
+  for (int k = threadIdx.x; k < nk; k += DT) {
     const double v = cs[it.c0 + k].coef;
     const float ch = (float)v;
     cf[k] = make_float2(ch, (float)(v - (double)ch));
@@ -190,14 +190,7 @@ __global__ void __launch_bounds__(DT) gather_digits_kernel(const GItem* __restri
     for (int i = 0; i < 2 * PP; ++i) { h[i] = 0.f; l[i] = 0.f; }
     for (int k = it.c0; k < it.c1; ++k) {
       const GContrib cb = cs[k];
-      float ch, cl;
-      if (k - it.c0 < GMAXK) {
-        ch = cf[k - it.c0].x;
-        cl = cf[k - it.c0].y;
-      } else {
-        ch = (float)cb.coef;
-        cl = (float)(cb.coef - (double)ch);
-      }
+      const float ch = cf[k - it.c0].x, cl = cf[k - it.c0].y;
       const float2* s = reinterpret_cast<const float2*>(sel_base(bs, slot_of(cb.src))) + off_of(cb.src) +
                         (long long)r * cb.src_rs;
       const bool al16 = (reinterpret_cast<uintptr_t>(s) & 15) == 0;
@@ -274,5 +267,6 @@ cudaError_t launch_gather_digits(const DevGather& g, const Bases& b, cudaStream_
 }
 
 int gather_digits_max_cols() { return GMAXC; }
+int gather_digits_max_contribs() { return GMAXK; }
 
 }  // namespace tt

@@ -440,6 +440,9 @@ struct Eng {
       for (const GItem& it : h.s2.items) {
         if (it.cols > gather_digits_max_cols())
           throw Err{TT_ERR_INVALID_ARG, "exact split: a sector longer than " + std::to_string(gather_digits_max_cols())};
+        if (it.c1 - it.c0 > gather_digits_max_contribs())
+          throw Err{TT_ERR_INVALID_ARG, "exact split: more than " + std::to_string(gather_digits_max_contribs()) +
+                                            " MPO terms feed one W-gather item"};
         // the digit gather stores column pairs (a BF16 pair per 32-bit word;
         // an odd row's last pair ends in the row's zero padding)
         if (((it.dst & 0x00FFFFFFFFFFFFFFull) | (uint64_t)it.dst_rs | (uint64_t)h.t2_size) & 1)
@@ -798,9 +801,13 @@ struct Eng {
         ensure(c, r->tcerr, 16);
         CK(cudaMemsetAsync(r->tcerr.p, 0, 16, st));
       }
+      // one output form per launch (the digit kernel is specialised on it)
+      const bool pair = !g.host.groups.empty() && (g.host.groups[0].flags & 2);
+      for (const GGroup& gg : g.host.groups)
+        if (((gg.flags & 2) != 0) != pair) throw Err{TT_ERR_STATE, "exact split: mixed output forms in one GEMM plan"};
       const long e = prof_begin(kind, g.d.flops);
       CK(launch_gemm_tcz(g.d.groups, g.d.segs, (const GTile*)g.tilesp.p, g.ntilesp, g.maps.p, b, (int*)r->tcerr.p,
-                         c->wait_ns, st));
+                         c->wait_ns, pair, st));
       prof_end(e);
       count();
       return;

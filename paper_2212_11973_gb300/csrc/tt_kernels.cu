@@ -124,9 +124,24 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(const GGroup* __restrict_
 // per operation, K 2^-46 of sum |a| |b| per output.  Output FP64.  Used by the
 // mixed modes' CholeskyQR Gram and apply GEMMs.
 // ---------------------------------------------------------------------------
+// v = hi + lo: hi the top 24 significant bits of v (truncated), lo the other
+// 29 rounded to 24 (error <= 2^-47 |v|), by integer operations on the FP64 bit
+// pattern (no FP64 arithmetic); zero for zero and FP64 subnormals, FP64
+// conversions for |v| outside [2^-97, 2^127]
 __device__ __forceinline__ float2 df_split(double v) {
-  const float h = __double2float_rn(v);
-  return make_float2(h, __double2float_rn(v - (double)h));
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return make_float2(0.f, 0.f);
+  if (e < 926 || e > 1150) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+  }
+  const unsigned sg = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sg | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+  // low 29 mantissa bits times 2^(e - 1075) = (ml 2^-29) 2^(e - 1046), e - 1046 >= -120
+  const float lo = ((float)(unsigned)(b & 0x1FFFFFFFull) * 1.862645149230957e-09f) *
+                   __uint_as_float((unsigned)(e - 1046 + 127) << 23);
+  return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sg));
 }
 
 __global__ void __launch_bounds__(256) gemm_df_kernel(const GGroup* __restrict__ groups, const GSeg* __restrict__ segs,

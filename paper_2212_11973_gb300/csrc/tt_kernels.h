@@ -112,17 +112,19 @@ cudaError_t launch_gemm_tcp(const GGroup* groups, const GSeg* segs, const GTile*
 // Exact-accumulation split GEMM on tcgen05 (tt_tcgen05z.cu): digit operands
 // (4 levels + int16 row exponents, GSeg.eA / eB), persistent 128 x 64 tiles,
 // the same maps; segments of K <= tcz_max_k(); output FP64 or two-float pairs
-// (flags bit 1).
+// (flags bit 1, the same in every group of a launch: pair).
 int tcz_max_k();
 size_t tcz_smem_bytes();
 cudaError_t launch_gemm_tcz(const GGroup* groups, const GSeg* segs, const GTile* tiles128x64, int ntiles,
-                            const void* maps, const Bases& b, int* err, long long wait_ns, cudaStream_t s);
+                            const void* maps, const Bases& b, int* err, long long wait_ns, bool pair, cudaStream_t s);
 // Digit producers (tt_digits.cu): FP64 rows -> digit rows; the W-gather of
 // the exact path (two-float S1 outputs -> digit rows of T2, rows up to
-// gather_digits_max_cols() long).
+// gather_digits_max_cols() long, at most gather_digits_max_contribs() MPO
+// terms per item).
 cudaError_t launch_digit_copy(const DevDigit& d, const Bases& b, cudaStream_t s);
 cudaError_t launch_gather_digits(const DevGather& g, const Bases& b, cudaStream_t s);
 int gather_digits_max_cols();
+int gather_digits_max_contribs();
 // err: set to 1 by a CTA whose bounded wait (budget wait_ns) ran out.
 cudaError_t launch_gemm_tc(const GGroup* groups, const GSeg* segs, const GTile* tiles128, int ntiles,
                            const void* maps, const Bases& b, int nsplit, int* err, long long wait_ns, cudaStream_t s);

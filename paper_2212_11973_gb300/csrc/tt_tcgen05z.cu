@@ -115,6 +115,10 @@ __device__ __forceinline__ void pair_of(int p, int& s, int& t) {
   t = d - s;
 }
 
+// PAIR: every group of the launch writes two-float pairs (flags bit 1), else
+// FP64 (accumulating with flags bit 0); one kernel per output form keeps the
+// FP64 conversions out of the pair kernel entirely
+template <bool PAIR>
 __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __restrict__ groups,
                                                                const GSeg* __restrict__ segs,
                                                                const GTile* __restrict__ tiles, int ntiles,
@@ -310,14 +314,12 @@ __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __r
       // the finished 32 x 32 block, 16 columns at a time through this warp's
       // staging buffer: one row per lane on the way in, 16 lanes per row (128
       // contiguous bytes) on the way out
-      const bool accum = g.flags & 1, out_pair = g.flags & 2;
+      const bool accum = g.flags & 1;
       const int c_l = lane & 15;
       uint64_t* const Cb = reinterpret_cast<uint64_t*>(sel_base(bs, slot_of(g.C))) + off_of(g.C);
 #pragma unroll
       for (int cb = 0; cb < 32; cb += 16) {
-        // two separate loops: a select inside one would run the FP64
-        // conversions (GB300: ~2 per clock per SM) for pair outputs too
-        if (out_pair) {
+        if (PAIR) {
 #pragma unroll
           for (int i = 0; i < 16; ++i)
             stg[lane * 16 + (i ^ (lane & 15))] =
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(ZTHREADS, 1) gemm_tcz_kernel(const GGroup* __r
           if (grow < g.M && col < g.N) {
             const long long o = (long long)grow * g.ldc + col;
             const uint64_t bits = stg[rr * 16 + (c_l ^ (rr & 15))];
-            if (out_pair || !accum) {
+            if (PAIR || !accum) {
               Cb[o] = bits;
             } else {
               double* Cp = reinterpret_cast<double*>(Cb + o);
@@ -381,14 +383,22 @@ int tcz_max_k() { return ZMAXK; }
 size_t tcz_smem_bytes() { return (size_t)ZSTAGES * ZSTAGE_BYTES + ZSTG_BYTES + 1024; }
 
 cudaError_t launch_gemm_tcz(const GGroup* groups, const GSeg* segs, const GTile* tiles, int ntiles, const void* maps,
-                            const Bases& b, int* err, long long wait_ns, cudaStream_t s) {
+                            const Bases& b, int* err, long long wait_ns, bool pair, cudaStream_t s) {
   if (ntiles == 0) return cudaSuccess;
   const size_t smem = tcz_smem_bytes();
-  static const cudaError_t e =
-      cudaFuncSetAttribute(gemm_tcz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static const cudaError_t e1 =
+      cudaFuncSetAttribute(gemm_tcz_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static const cudaError_t e2 =
+      cudaFuncSetAttribute(gemm_tcz_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e1 != cudaSuccess) return e1;
+  if (e2 != cudaSuccess) return e2;
   const int grid = ntiles < sm_count_z() ? ntiles : sm_count_z();
-  gemm_tcz_kernel<<<grid, ZTHREADS, smem, s>>>(groups, segs, tiles, ntiles, (const CUtensorMap*)maps, b, err, wait_ns);
+  if (pair)
+    gemm_tcz_kernel<true><<<grid, ZTHREADS, smem, s>>>(groups, segs, tiles, ntiles, (const CUtensorMap*)maps, b, err,
+                                                       wait_ns);
+  else
+    gemm_tcz_kernel<false><<<grid, ZTHREADS, smem, s>>>(groups, segs, tiles, ntiles, (const CUtensorMap*)maps, b, err,
+                                                        wait_ns);
   return cudaGetLastError();
 }
 
