@@ -871,25 +871,48 @@ struct CholF64 {
   static __device__ __forceinline__ T of(double x) { return x; }
   static __device__ __forceinline__ double dbl(T a) { return a; }
   static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T add(T a, double v) { return a + v; }
+  // |a - target| (a test against a threshold)
+  static __device__ __forceinline__ double dev(T a, double target) { return fabs(a - target); }
   // a - b c
   static __device__ __forceinline__ T fnms(T a, T b, T c) { return fma(-b, c, a); }
-  static __device__ __forceinline__ T mul(T a, double s) { return a * s; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
 };
+
+// FP64 value of a normal float by integer operations (exponent rebias and
+// mantissa shift); zero for zero and float subnormals
+__device__ __forceinline__ double dbl_of_float(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFF;
+  if (e == 0) return 0.0;
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
 
 struct CholDF {
   using T = float2;  // value x + y, |y| <= ulp(x) / 2
   // unit roundoff of the double-float Gram (gemm_df_kernel) and factor
   static constexpr double u = 1.4210854715202004e-14;  // 2^-46
-  static __device__ __forceinline__ T of(double v) {
-    const float h = (float)v;
-    return make_float2(h, (float)(v - (double)h));
-  }
-  static __device__ __forceinline__ double dbl(T a) { return (double)a.x + (double)a.y; }
+  static __device__ __forceinline__ T of(double v) { return df_split(v); }
+  // one FP64 addition (the conversions are integer operations)
+  static __device__ __forceinline__ double dbl(T a) { return dbl_of_float(a.x) + dbl_of_float(a.y); }
   static __device__ __forceinline__ T zero() { return make_float2(0.f, 0.f); }
   static __device__ __forceinline__ T two_sum(float s, float t) {
     const float h = s + t;
     const float bp = h - s;
     return make_float2(h, (s - (h - bp)) + (t - bp));
+  }
+  static __device__ __forceinline__ T add(T a, double v) {
+    const float2 b = df_split(v);
+    const float s = a.x + b.x;
+    const float bp = s - a.x;
+    const float t = ((a.x - (s - bp)) + (b.x - bp)) + (a.y + b.y);
+    return two_sum(s, t);
+  }
+  static __device__ __forceinline__ double dev(T a, double target) {
+    return (double)fabsf((a.x - (float)target) + a.y);
   }
   static __device__ __forceinline__ T fnms(T a, T b, T c) {
     const float p = b.x * c.x;
@@ -902,12 +925,11 @@ struct CholDF {
     t += a.y - e;
     return two_sum(s, t);
   }
-  static __device__ __forceinline__ T mul(T a, double v) {
-    const float sh = (float)v, sl = (float)(v - (double)sh);
-    const float p = a.x * sh;
-    float e = fmaf(a.x, sh, -p);
-    e = fmaf(a.x, sl, e);
-    e = fmaf(a.y, sh, e);
+  static __device__ __forceinline__ T mul(T a, T b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
     return two_sum(p, e);
   }
 };
@@ -932,15 +954,16 @@ __global__ void __launch_bounds__(CHOL_T, 1) chol_inv_smem_kernel(const CholJob*
   double* Ri = ws + J.ri;
   const long long nn = (long long)n * n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
-  __shared__ double piv, red[CHOL_T / 32];
+  __shared__ double red[CHOL_T / 32];
+  __shared__ T piv_t, ipiv_t;  // the current pivot and its reciprocal
   __shared__ int bad;
   // G = sum of the partial Gram matrices, upper triangle into shared memory
   for (int i = warp; i < n; i += nw)
     for (int j = i + lane; j < n; j += 32) {
       const long long e = (long long)i * n + j;
-      double acc = G[e];
-      for (int s = 1; s < J.parts; ++s) acc += G[s * nn + e];
-      sm[pk(i, j, n)] = A::of(acc);
+      T acc = A::of(G[e]);
+      for (int s = 1; s < J.parts; ++s) acc = A::add(acc, G[s * nn + e]);
+      sm[pk(i, j, n)] = acc;
     }
   __syncthreads();
   if (J.shift == 2) {
@@ -949,7 +972,7 @@ __global__ void __launch_bounds__(CHOL_T, 1) chol_inv_smem_kernel(const CholJob*
     double mx = 0.0;
     for (int i = warp; i < n; i += nw)
       for (int j = i + lane; j < n; j += 32) {
-        const double dev = fabs(A::dbl(sm[pk(i, j, n)]) - (i == j ? 1.0 : 0.0));
+        const double dev = A::dev(sm[pk(i, j, n)], i == j ? 1.0 : 0.0);
         mx = (dev <= mx) ? mx : (dev == dev ? dev : 1e300);
       }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -962,21 +985,22 @@ __global__ void __launch_bounds__(CHOL_T, 1) chol_inv_smem_kernel(const CholJob*
       return;
     }
     if ((double)n * all <= 1e-8) {
-      for (long long e = tid; e < nn; e += blockDim.x) {
-        const int i = (int)(e / n), j = (int)(e % n);
-        if (j < i) {
-          R[e] = 0.0;
-          Ri[e] = 0.0;
-        } else if (j == i) {
-          const double h = 0.5 * (A::dbl(sm[pk(i, i, n)]) - 1.0);
-          R[e] = 1.0 + h;
-          Ri[e] = 1.0 - h;
-        } else {
-          const double g = A::dbl(sm[pk(i, j, n)]);
-          R[e] = g;
-          Ri[e] = -g;
+      for (int i = warp; i < n; i += nw)
+        for (int j = lane; j < n; j += 32) {
+          const long long e = (long long)i * n + j;
+          if (j < i) {
+            R[e] = 0.0;
+            Ri[e] = 0.0;
+          } else if (j == i) {
+            const double h = 0.5 * (A::dbl(sm[pk(i, i, n)]) - 1.0);
+            R[e] = 1.0 + h;
+            Ri[e] = 1.0 - h;
+          } else {
+            const double g = A::dbl(sm[pk(i, j, n)]);
+            R[e] = g;
+            Ri[e] = -g;
+          }
         }
-      }
       return;
     }
   }
@@ -999,12 +1023,13 @@ __global__ void __launch_bounds__(CHOL_T, 1) chol_inv_smem_kernel(const CholJob*
         bad = 1;
         fail[J.sec] = 1;
       }
-      piv = bad ? 1.0 : sqrt(d);
+      const double p = bad ? 1.0 : sqrt(d);
+      piv_t = A::of(p);
+      ipiv_t = A::of(1.0 / p);
     }
     __syncthreads();
     if (bad) return;
-    const double p = piv, ip = 1.0 / p;
-    for (int j = k + tid; j < n; j += blockDim.x) sm[pk(k, j, n)] = j == k ? A::of(p) : A::mul(sm[pk(k, j, n)], ip);
+    for (int j = k + tid; j < n; j += blockDim.x) sm[pk(k, j, n)] = j == k ? piv_t : A::mul(sm[pk(k, j, n)], ipiv_t);
     __syncthreads();
     for (int i = k + 1 + warp; i < n; i += nw) {
       const T rki = sm[pk(k, i, n)];
@@ -1012,17 +1037,14 @@ __global__ void __launch_bounds__(CHOL_T, 1) chol_inv_smem_kernel(const CholJob*
     }
     __syncthreads();
   }
-  for (long long e = tid; e < nn; e += blockDim.x) {
-    const int i = (int)(e / n), j = (int)(e % n);
-    R[e] = (j >= i) ? A::dbl(sm[pk(i, j, n)]) : 0.0;
-  }
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) R[(long long)i * n + j] = (j >= i) ? A::dbl(sm[pk(i, j, n)]) : 0.0;
   // in-place inverse, rows from the bottom
   for (int k = n - 1; k >= 0; --k) {
     __syncthreads();
-    if (tid == 0) piv = 1.0 / A::dbl(sm[pk(k, k, n)]);
+    if (tid == 0) ipiv_t = A::of(1.0 / A::dbl(sm[pk(k, k, n)]));
     __syncthreads();
-    const double ik = piv;
-    for (int c = k + tid; c < n; c += blockDim.x) sm[pk(k, c, n)] = c == k ? A::of(ik) : A::mul(sm[pk(k, c, n)], ik);
+    for (int c = k + tid; c < n; c += blockDim.x) sm[pk(k, c, n)] = c == k ? ipiv_t : A::mul(sm[pk(k, c, n)], ipiv_t);
     __syncthreads();
     for (int i = warp; i < k; i += nw) {
       const T rik = sm[pk(i, k, n)];
@@ -1032,10 +1054,8 @@ __global__ void __launch_bounds__(CHOL_T, 1) chol_inv_smem_kernel(const CholJob*
     }
   }
   __syncthreads();
-  for (long long e = tid; e < nn; e += blockDim.x) {
-    const int i = (int)(e / n), j = (int)(e % n);
-    Ri[e] = (j >= i) ? A::dbl(sm[pk(i, j, n)]) : 0.0;
-  }
+  for (int i = warp; i < n; i += nw)
+    for (int j = lane; j < n; j += 32) Ri[(long long)i * n + j] = (j >= i) ? A::dbl(sm[pk(i, j, n)]) : 0.0;
 }
 
 __global__ void dot_finalize(const double* partial, int nblk, double* out) {

@@ -415,18 +415,27 @@ int h_qr_left(int nl, int nr, const int* qn, const int* qs, const int* qd, const
       double* Ri = &Sx.at(mkref(S_AUX2, J.ri), 0);
       const int64_t nn = (int64_t)n * n;
       Sx.at(mkref(S_AUX2, J.g), (int64_t)J.parts * nn - 1);  // bounds of the partials
+      // the device keeps the summed upper triangle packed row by row in the
+      // job's scratch (shared memory for small n); the scratch must not
+      // overlap anything still needed, so it is used here for every n
+      Sx.at(mkref(S_AUX2, J.pk), (int64_t)n * (n + 1) / 2 - 1);
+      double* Pk = &Sx.at(mkref(S_AUX2, J.pk), 0);
+      auto P = [&](int i, int j) -> double& { return Pk[(int64_t)i * n - (int64_t)i * (i - 1) / 2 + (j - i)]; };
       for (int i = 0; i < n; ++i)
-        for (int j = i; j < n; ++j)
-          for (int p = 1; p < J.parts; ++p) G[i * n + j] += G[p * nn + i * n + j];
+        for (int j = i; j < n; ++j) {
+          double acc = G[i * n + j];
+          for (int p = 1; p < J.parts; ++p) acc += G[p * nn + i * n + j];
+          P(i, j) = acc;
+        }
       if (J.shift == 2) {
         double mx = 0.0;
         for (int i = 0; i < n; ++i)
-          for (int j = i; j < n; ++j) mx = std::max(mx, std::fabs(G[i * n + j] - (i == j ? 1.0 : 0.0)));
+          for (int j = i; j < n; ++j) mx = std::max(mx, std::fabs(P(i, j) - (i == j ? 1.0 : 0.0)));
         if (!(mx <= 1e-3)) { fl[J.sec] = 1; return; }
         if (n * mx <= 1e-8) {
           for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) {
-              const double e = G[i * n + j];
+              const double e = j < i ? 0.0 : P(i, j);
               R[i * n + j] = j < i ? 0.0 : (j == i ? 1.0 + 0.5 * (e - 1.0) : e);
               Ri[i * n + j] = j < i ? 0.0 : (j == i ? 1.0 - 0.5 * (e - 1.0) : -e);
             }
@@ -435,18 +444,18 @@ int h_qr_left(int nl, int nr, const int* qn, const int* qs, const int* qd, const
       }
       if (J.shift == 1) {
         double tr = 0.0;
-        for (int i = 0; i < n; ++i) tr += G[i * n + i];
+        for (int i = 0; i < n; ++i) tr += P(i, i);
         const double sft = 11.0 * ((double)J.m * n + (double)n * (n + 1)) * 1.1102230246251565e-16 * tr;
-        for (int i = 0; i < n; ++i) G[i * n + i] += sft;
+        for (int i = 0; i < n; ++i) P(i, i) += sft;
       }
       for (int64_t e = 0; e < nn; ++e) R[e] = 0.0;
       for (int k = 0; k < n; ++k) {
-        const double d = G[k * n + k];
+        const double d = P(k, k);
         if (!(d > 0.0)) { fl[J.sec] = 1; return; }
         const double pv = std::sqrt(d);
-        for (int j = k; j < n; ++j) R[k * n + j] = G[k * n + j] / pv;
+        for (int j = k; j < n; ++j) R[k * n + j] = P(k, j) / pv;
         for (int i = k + 1; i < n; ++i)
-          for (int j = i; j < n; ++j) G[i * n + j] -= R[k * n + i] * R[k * n + j];
+          for (int j = i; j < n; ++j) P(i, j) -= R[k * n + i] * R[k * n + j];
       }
       for (int j = 0; j < n; ++j) {
         for (int i = j + 1; i < n; ++i) Ri[i * n + j] = 0.0;
