@@ -190,6 +190,53 @@ int h_exact_exponents(const int* geom, const double* par, int j, const int* nsec
   });
 }
 
+// The exact split's digit W-gather items of site j, against what the kernel
+// assumes: rows of at most max_cols columns, at most max_contribs MPO terms per
+// item, even BF16 offsets and strides (it stores column pairs as one 32-bit
+// word), every T2 element written by exactly one item, and the extra column
+// an odd-width row's last pair writes lying in that row's own zero padding
+// (not in another item's columns).  stats: [max cols, max terms per item,
+// items with an odd width].
+int h_gather_digit_items(const int* geom, const double* par, int j, const int* nsec_lr, const int* qn, const int* qs,
+                         const int* qd, int max_cols, int max_contribs, int* stats) {
+  return guarded([&] {
+    Mpo M = model(geom, par);
+    Bond BL = bond_from(qn, qs, qd, nsec_lr[0]);
+    Bond BR = bond_from(qn + nsec_lr[0], qs + nsec_lr[0], qd + nsec_lr[0], nsec_lr[1]);
+    SitePlanHost P = build_site_plan(BL, BR, M.ls, M.site[j].terms, M.chan[j], M.chan[j + 1], true, true);
+    if (P.t2_size & 1) throw std::runtime_error("odd T2 level stride");
+    std::vector<char> owner((size_t)P.t2_size, 0);
+    int mc = 0, mk = 0, odd = 0;
+    for (const GItem& it : P.s2.items) {
+      const int64_t off = (int64_t)(it.dst & 0x00FFFFFFFFFFFFFFull);
+      if ((off | it.dst_rs) & 1) throw std::runtime_error("odd digit row offset or stride");
+      mc = std::max(mc, it.cols);
+      mk = std::max(mk, it.c1 - it.c0);
+      odd += it.cols & 1;
+      for (int r = 0; r < it.rows; ++r)
+        for (int c = 0; c < it.cols; ++c) {
+          const int64_t e = off + (int64_t)r * it.dst_rs + c;
+          if (e < 0 || e >= P.t2_size) throw std::runtime_error("T2 element outside the level");
+          if (owner[(size_t)e]) throw std::runtime_error("T2 element written by two items");
+          owner[(size_t)e] = 1;
+        }
+    }
+    for (const GItem& it : P.s2.items) {
+      if (!(it.cols & 1)) continue;
+      const int64_t off = (int64_t)(it.dst & 0x00FFFFFFFFFFFFFFull);
+      for (int r = 0; r < it.rows; ++r) {
+        const int64_t e = off + (int64_t)r * it.dst_rs + it.cols;
+        if (e >= P.t2_size || owner[(size_t)e]) throw std::runtime_error("pair store of an odd row leaves its padding");
+      }
+    }
+    if (mc > max_cols) throw std::runtime_error("row longer than the kernel's limit");
+    if (mk > max_contribs) throw std::runtime_error("more MPO terms per item than the kernel's limit");
+    stats[0] = mc;
+    stats[1] = mk;
+    stats[2] = odd;
+  });
+}
+
 const char* h_error() { return g_err.c_str(); }
 
 int h_mpo_shape(const int* geom, const double* par, int* N, int* chan_dims, int cap) {

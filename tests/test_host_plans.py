@@ -374,3 +374,23 @@ def test_exact_split_exponents_follow_their_rows(h, geo, j, D):
     qn, qs, qd = _secs_arrays(SL, SR)
     h.h_exact_exponents.argtypes = [_PI, _PD, C.c_int, _PI, _PI, _PI, _PI]
     _chk(h, h.h_exact_exponents(m.geom, m.par, j, _ia([len(SL), len(SR)]), qn, qs, qd))
+
+
+@pytest.mark.parametrize("geo,j,D", CASES + [((6, 6, True, 1), 17, 200)])
+def test_digit_gather_items_fit_the_kernel(h, geo, j, D):
+    """The digit W-gather (two columns per lane, 32-bit stores of BF16 pairs,
+    MPO coefficient splits in a 64-entry shared table) relies on plan
+    properties the host also checks before a launch: rows of at most 256
+    columns, at most 64 MPO terms per item, even BF16 offsets, disjoint items,
+    and an odd row's extra column inside its own zero padding.  Includes a
+    6-wide cylinder site (the widest MPO of the workloads) with odd-width
+    sectors."""
+    Lx, Wy, per, form = geo
+    m = Model(h, Lx, Wy, per, 1.0, 8.0, -2.48, form, TP.get(geo, 0.0))
+    SL, SR = _random_bonds(D, 29 + j)
+    qn, qs, qd = _secs_arrays(SL, SR)
+    stats = _ia([0, 0, 0])
+    h.h_gather_digit_items.argtypes = [_PI, _PD, C.c_int, _PI, _PI, _PI, _PI, C.c_int, C.c_int, _PI]
+    _chk(h, h.h_gather_digit_items(m.geom, m.par, j, _ia([len(SL), len(SR)]), qn, qs, qd, 256, 64, stats))
+    assert 0 < stats[0] <= 256 and 0 < stats[1] <= 64
+    assert stats[2] > 0  # odd widths occur, so the padding rule is exercised
