@@ -54,21 +54,32 @@ typedef enum {
 
 typedef enum {
   TT_PREC_FP64 = 0,          /* every contraction in FP64 */
-  TT_PREC_MIXED_BF16X3 = 1,  /* H_eff and environment contractions as split-
-                                BF16 tensor-core products, 2 levels / 3
-                                products (~2^-16 relative) */
+  TT_PREC_MIXED_BF16X3 = 1,  /* H_eff and bond contractions as split-BF16
+                                tensor-core products, 2 levels / 3 products
+                                (~2^-16 relative); environment updates per
+                                env_precision */
   TT_PREC_MIXED_BF16X6 = 2,  /* 3 levels / 6 products (~2^-24 relative), FP32
                                 accumulation folded per K chunk into a two-
-                                float sum.  In both mixed modes the Lanczos
-                                vectors, Krylov exponential, QR, SVD, absorb
-                                step, measurements and log-norm stay FP64 */
-  TT_PREC_SPLIT_EXACT = 3    /* FP64 operands cut per 32-wide K tile into four
-                                fixed-point BF16 digits (per-row / per-column
-                                exponent), tensor-core products summed exactly
-                                in FP32 per tile and folded into a two-float
-                                accumulator (Ozaki scheme): ~2^-32 of the
-                                operands' row/column bounds; FP64 layouts, FP64
-                                W-gather */
+                                float sum.  In both modes the Lanczos vectors,
+                                Krylov exponential, SVD, absorb step,
+                                measurements and log-norm stay FP64; the
+                                CholeskyQR gauge runs in double-float (~2^-46)
+                                with a FP64 Householder fallback */
+  TT_PREC_SPLIT_EXACT = 3    /* exact-accumulation split (Ozaki scheme): the
+                                H_eff and bond applies' operands as four
+                                fixed-point BF16 digits with one exponent per
+                                row and GEMM segment (K <= 256), the ten digit
+                                products with s + t <= 3 summed exactly in FP32
+                                on the tcgen05 tensor cores and folded into a
+                                two-float accumulator per segment: ~2^-32 of the
+                                rows' bounds; the W-gather in two-float
+                                arithmetic writing digit rows.  Sectors must
+                                have at most 256 states and a gather item at
+                                most 64 MPO terms (TT_ERR_INVALID_ARG
+                                otherwise).  Environment updates per
+                                env_precision; the CholeskyQR gauge in
+                                double-float; Lanczos, Krylov exponential,
+                                absorb, measurements and log-norm in FP64 */
 } tt_precision;
 
 typedef struct tt_ctx tt_ctx;
