@@ -175,7 +175,8 @@ __global__ void __launch_bounds__(DT) gather_digits_kernel(const GItem* __restri
   // the item's MPO coefficients as float pairs, split once per CTA (FP64
   // arithmetic runs at ~1/64 of FP32 on GB300)
   __shared__ float2 cf[GMAXK];
-  const int nk = it.c1 - it.c0;
+  // the host rejects items with more terms; the clamp keeps the table in bounds
+  const int nk = min(it.c1 - it.c0, GMAXK);
   for (int k = threadIdx.x; k < nk; k += DT) {
     const double v = cs[it.c0 + k].coef;
     const float ch = (float)v;
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(DT) gather_digits_kernel(const GItem* __restri
     float h[2 * PP], l[2 * PP];
 #pragma unroll
     for (int i = 0; i < 2 * PP; ++i) { h[i] = 0.f; l[i] = 0.f; }
-    for (int k = it.c0; k < it.c1; ++k) {
+    for (int k = it.c0; k < it.c0 + nk; ++k) {
       const GContrib cb = cs[k];
       const float ch = cf[k - it.c0].x, cl = cf[k - it.c0].y;
       const float2* s = reinterpret_cast<const float2*>(sel_base(bs, slot_of(cb.src))) + off_of(cb.src) +
