@@ -569,7 +569,10 @@ def main():
         peak_note = "of measured (bf16 sustained, MEASURED_PEAKS.json)"
     else:
         peak, peak_note = 1700.0, "of fallback"
-    roofline = {"bound": "tensor", "kernel": "site H_eff split-BF16 GEMMs (S1 + S3)",
+    kernel_name = {0: "site H_eff FP64 GEMMs (S1 + S3)", 1: "site H_eff split-BF16 GEMMs (S1 + S3)",
+                   2: "site H_eff split-BF16 GEMMs (S1 + S3)",
+                   3: "site H_eff exact-split digit GEMMs (S1 + S3, gemm_tcz_kernel)"}[prec]
+    roofline = {"bound": "tensor", "kernel": kernel_name,
                 "achieved": heff_tflops, "peak": peak, "unit": "TFLOP/s",
                 "frac": (heff_tflops / peak) if heff_tflops else None,
                 "flops_per_launch": flops / max(heff_n, 1), "avg_launch_ms": heff_ms / max(heff_n, 1),
@@ -577,7 +580,9 @@ def main():
                 "peak_note": peak_note, "traffic": None,
                 "measured_in": f"profiled pass of {nprof} graph-replayed beta-steps after the timed region "
                                "(event pairs around each launch on the library stream)",
-                "traffic_note": "null: no ncu capture of this state's kernels since they last changed"}
+                "traffic_note": "null: this state's graph-replayed kernels are not captured under ncu; the same "
+                                "kernels on bench.py --workload heff-apply (Gaussian sectors, D=1024) move "
+                                "their algorithmic bytes (profiles/gemm_tcz_kernel_heff_apply_D1024_exact.md)"}
     cpu = None if args.no_cpu_baseline else cpu_baseline()
     line = {
         "metric": METRIC, "value": per_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
