@@ -43,3 +43,36 @@ def test_missing_library_fails_loudly(tmp_path):
             tantrg.load_library(str(tmp_path / "absent.so"))
         finally:
             tantrg._lib = saved
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding marshals has the header's size and field
+    offsets (a C program compiled against include/tantrg.h prints them)."""
+    import shutil
+    import subprocess
+    import pytest
+    from paper_2212_11973_gb300 import tantrg
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {n: getattr(tantrg, n) for n in ("tt_alloc_cb", "tt_model", "tt_run_opts", "tt_obs", "tt_stats")}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "tantrg.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for l in out:
+        if l.strip():
+            s, f, v = l.split()
+            got[(s, f)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
